@@ -1,0 +1,150 @@
+/*
+ * pb.h -- C ABI of the GB300 direct-sum boundary-integral linear
+ * Poisson-Boltzmann library (the well-conditioned formulation of Geng & Jacob,
+ * "A GPU-accelerated Direct-sum Boundary Integral Poisson-Boltzmann Solver").
+ *
+ * The problem (Section 1, Eqs. (1)-(4)): a solute region Omega_1 with dielectric
+ * constant eps1 holding Nc point charges, bounded by a closed surface Gamma,
+ * inside a solvent with dielectric constant eps2 and inverse Debye length
+ * kappa.  Gamma is given as N flat triangles with centroid collocation
+ * (Section 2.2): centroid x_i, unit outward normal nu_i, area W_i.
+ *
+ * The unknowns are u = [phi_1..phi_N, dphi/dnu_1..dphi/dnu_N] at the centroids;
+ * the system A u = b is Eqs. (12)-(13) with the kernels K1..K4 of Eq. (10)
+ * (eps = eps2/eps1), and b = [S1(x_i); S2(x_i)] of Eq. (11) with each charge
+ * divided by eps1.  The electrostatic solvation energy is Eq. (14), reported in
+ * kcal/mol (332.0636 kcal/mol per e_c^2/(4 pi eps_0 Angstrom)).
+ *
+ * Conventions for every entry point:
+ *  - Lengths in Angstrom, charges in e_c, energies in kcal/mol.
+ *  - Vectors of length 2N are FP64, contiguous, device memory owned by the
+ *    caller (for example a torch tensor's data_ptr()).
+ *  - All GPU work of a context runs on the CUDA stream given to pb_create.
+ *    pb_matvec and pb_source only enqueue work; pb_solve, pb_energy,
+ *    pb_energy_of and pb_create return after the stream has finished the work
+ *    they enqueued.
+ *  - Every call returns a pb_status and never aborts, traps or exits.  On
+ *    failure pb_last_error(ctx) (or pb_last_error(NULL) when no context
+ *    exists) holds a one-line message.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef PB_H
+#define PB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pb_ctx pb_ctx;   /* opaque; owns all the device memory it allocates */
+
+typedef enum {
+    PB_OK = 0,
+    PB_ERR_ARG = 1,       /* invalid argument (NULL pointer, N <= 0, eps <= 0, ...) */
+    PB_ERR_BADMESH = 2,   /* area <= 0 or non-finite, normal far from unit length,
+                             or the Gauss orientation check failed */
+    PB_ERR_OOM = 3,       /* device allocation failed */
+    PB_ERR_CUDA = 4,      /* a CUDA runtime call failed */
+    PB_ERR_NOCONV = 5,    /* GMRES reached maxit without meeting tol */
+    PB_ERR_NAN = 6,       /* a non-finite residual or Hessenberg entry appeared */
+    PB_ERR_TIMEOUT = 7,   /* a bounded wait gave up */
+    PB_ERR_ADMIT = 8      /* a request does not fit the memory budget */
+} pb_status;
+
+typedef enum {
+    PB_FP64 = 0,          /* every pair in FP64, FP64 accumulation */
+    PB_FP32PAIR = 1       /* pair arithmetic in FP32 (hardware rsqrt/exp2),
+                             FP32 partial sums per source tile, FP64 row sums */
+} pb_precision;
+
+typedef struct {
+    int restart;          /* GMRES restart length m (>= 1); 10 if 0 */
+    double tol;           /* stop when ||b - A x||_2 / ||b||_2 <= tol; 1e-4 if 0 */
+    int maxit;            /* maximum Arnoldi steps (products with A); 1000 if 0 */
+    pb_precision prec;    /* precision of the products with A inside GMRES */
+    int refine;           /* number of FP64 iterative-refinement steps after a
+                             PB_FP32PAIR solve: r = b - A_fp64 x, solve A d = r
+                             with the same options, x += d.  0 = none */
+} pb_solve_opts;
+
+typedef struct {
+    int iters;            /* Arnoldi steps taken, all refinement passes included */
+    int cycles;           /* GMRES restart cycles */
+    double rel_resid;     /* final true relative residual, in the precision of
+                             the last product used to measure it */
+    double energy_kcal;   /* E_sol of Eq. (14) for the solution, FP64 reduction */
+    double rel_resid_fp64;/* ||b - A_fp64 x|| / ||b|| when refine > 0, else -1 */
+    int refine_steps;     /* refinement steps taken */
+} pb_solve_info;
+
+typedef struct {
+    int64_t n;            /* triangles */
+    int64_t nc;           /* charges */
+    double eps1, eps2, kappa;
+    double center[3];     /* the shift subtracted from every coordinate (bounding-box centre) */
+    double gauss_min, gauss_max; /* min / max over charges of sum_j W_j dG0(x_k, x_j)/dnu_j
+                                    (about -1 for charges inside a closed outward surface) */
+    int64_t device_bytes; /* device memory held by the context */
+} pb_ctx_info;
+
+/* Create a context for one surface and one charge set (Sections 2.2 and 2.4).
+ * centroids, normals: N x 3 row-major; areas: N; charges: Nc x 4 rows (x, y, z, Q).
+ * Each pointer may be host or device memory (detected per pointer); the data
+ * are copied, the caller keeps ownership.  The geometry is validated (areas
+ * finite and > 0, normals within 1e-3 of unit length; normals are then
+ * renormalised), shifted by the bounding-box centre, packed into FP64 and FP32
+ * device arrays, and checked for orientation: every charge must see a Gauss
+ * sum in (-1.5, -0.5).  Nc may be 0 (then charges may be NULL).
+ * cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
+ * Errors: PB_ERR_ARG, PB_ERR_BADMESH, PB_ERR_OOM, PB_ERR_CUDA; *out is NULL then. */
+pb_status pb_create(const double *centroids, const double *normals, const double *areas, int64_t N,
+                    const double *charges, int64_t Nc, double eps1, double eps2, double kappa,
+                    void *cuda_stream, pb_ctx **out);
+
+/* Replace the charge set (a new right-hand side on the same surface; Eq. (11)).
+ * Same pointer rules as pb_create.  Invalidates the stored solution. */
+pb_status pb_set_charges(pb_ctx *ctx, const double *charges, int64_t Nc);
+
+/* b = [S1(x_i); S2(x_i)] of Eq. (11) into the caller's device buffer b (2N). */
+pb_status pb_source(pb_ctx *ctx, double *b, pb_precision prec);
+
+/* y = A u, Eqs. (12)-(13).  u, y: device, 2N each, must not overlap.  Enqueued
+ * on the context's stream.  Uses the context's scratch memory, so calls on one
+ * context are serialised by its stream. */
+pb_status pb_matvec(pb_ctx *ctx, const double *u, double *y, pb_precision prec);
+
+/* Solve A u = b with restarted GMRES on the device (Section 2.4; x0 = 0 unless
+ * x0 is given, restarts continue from the current approximation), then
+ * evaluate Eq. (14).  x0: device 2N or NULL.  x_out: device 2N or NULL; the
+ * solution is also kept in the context for pb_energy.  info may be NULL.
+ * Returns PB_ERR_NOCONV (solution and info still filled) if maxit is reached. */
+pb_status pb_solve(pb_ctx *ctx, const pb_solve_opts *opts, const double *x0, double *x_out,
+                   pb_solve_info *info);
+
+/* Eq. (14) for the solution of the last successful pb_solve, FP64 pairs. */
+pb_status pb_energy(pb_ctx *ctx, double *energy_kcal);
+
+/* Eq. (14) for an arbitrary device vector u (2N): (1/2) sum_k Q_k phi_reac(x_k). */
+pb_status pb_energy_of(pb_ctx *ctx, const double *u, pb_precision prec, double *energy_kcal);
+
+/* Context facts (sizes, centring shift, Gauss orientation sums, memory). */
+pb_status pb_get_info(pb_ctx *ctx, pb_ctx_info *info);
+
+/* Free all device memory of the context.  NULL is accepted. */
+void pb_destroy(pb_ctx *ctx);
+
+/* Static string for a status code. */
+const char *pb_status_string(pb_status s);
+
+/* Last error message of a context, or of the calling thread when ctx is NULL. */
+const char *pb_last_error(const pb_ctx *ctx);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t pb_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PB_H */

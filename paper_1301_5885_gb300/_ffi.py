@@ -1,0 +1,249 @@
+"""ctypes binding of include/pb.h: the same entry points under the same names.
+
+Argument marshalling only: every numerical step runs in libgabipb.so's CUDA
+kernels.  Device vectors are torch CUDA tensors (float64, contiguous); geometry
+and charges may be numpy arrays (host) or torch tensors (host or device).
+The library must have been built (``build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PB_OK, PB_ERR_ARG, PB_ERR_BADMESH, PB_ERR_OOM, PB_ERR_CUDA, PB_ERR_NOCONV, PB_ERR_NAN, PB_ERR_TIMEOUT, PB_ERR_ADMIT = range(9)
+PB_FP64, PB_FP32PAIR = 0, 1
+PRECISIONS = {"fp64": PB_FP64, "fp32pair": PB_FP32PAIR, PB_FP64: PB_FP64, PB_FP32PAIR: PB_FP32PAIR}
+
+
+class PBError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_string(status)}: {message}")
+        self.status = status
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("prec", ctypes.c_int), ("refine", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("rel_resid", ctypes.c_double),
+                ("energy_kcal", ctypes.c_double), ("rel_resid_fp64", ctypes.c_double),
+                ("refine_steps", ctypes.c_int)]
+
+
+class _CtxInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nc", ctypes.c_int64), ("eps1", ctypes.c_double),
+                ("eps2", ctypes.c_double), ("kappa", ctypes.c_double), ("center", ctypes.c_double * 3),
+                ("gauss_min", ctypes.c_double), ("gauss_max", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
+# Every symbol include/pb.h declares, with (restype, argtypes).
+_VP, _D, _I64, _I = ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int
+SIGNATURES = {
+    "pb_create": (_I, [_VP, _VP, _VP, _I64, _VP, _I64, _D, _D, _D, _VP, ctypes.POINTER(_VP)]),
+    "pb_set_charges": (_I, [_VP, _VP, _I64]),
+    "pb_source": (_I, [_VP, _VP, _I]),
+    "pb_matvec": (_I, [_VP, _VP, _VP, _I]),
+    "pb_solve": (_I, [_VP, ctypes.POINTER(_Opts), _VP, _VP, ctypes.POINTER(_Info)]),
+    "pb_energy": (_I, [_VP, ctypes.POINTER(_D)]),
+    "pb_energy_of": (_I, [_VP, _VP, _I, ctypes.POINTER(_D)]),
+    "pb_get_info": (_I, [_VP, ctypes.POINTER(_CtxInfo)]),
+    "pb_destroy": (None, [_VP]),
+    "pb_status_string": (ctypes.c_char_p, [_I]),
+    "pb_last_error": (ctypes.c_char_p, [_VP]),
+    "pb_kernel_launches": (ctypes.c_uint64, []),
+}
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libgabipb.so (it must already be built: no silent rebuild, no fallback)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: run paper_1301_5885_gb300.build.build() first "
+                              "(there is no CPU fallback for this library)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().pb_status_string(int(s)).decode()
+    except Exception:  # pragma: no cover - only when the library itself is unavailable
+        return f"status {s}"
+
+
+def pb_status_string(s: int) -> str:
+    return status_string(s)
+
+
+def pb_last_error(ctx=None) -> str:
+    h = ctx.handle if isinstance(ctx, Context) else ctx
+    msg = lib().pb_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def pb_kernel_launches() -> int:
+    return int(lib().pb_kernel_launches())
+
+
+def _check(status: int, ctx=None):
+    if status != PB_OK:
+        raise PBError(status, pb_last_error(ctx))
+
+
+def _ptr_f64(a, length: int | None = None, name: str = "array", keep=None):
+    """Pointer to float64 contiguous data from a numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64 or not a.is_contiguous():
+                a = a.to(torch.float64).contiguous()
+            if length is not None and a.numel() != length:
+                raise ValueError(f"{name}: expected {length} elements, got {a.numel()}")
+            if keep is not None:
+                keep.append(a)
+            return a.data_ptr()
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if length is not None and arr.size != length:
+        raise ValueError(f"{name}: expected {length} elements, got {arr.size}")
+    if keep is not None:
+        keep.append(arr)
+    return arr.ctypes.data
+
+
+def _device_vec(t, n2: int, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n2:
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of length {n2}")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Context:
+    """An owned pb_ctx handle."""
+
+    def __init__(self, handle, n: int, nc: int):
+        self.handle = handle
+        self.n = n
+        self.nc = nc
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        pb_destroy(self)
+
+    def __del__(self):
+        try:
+            pb_destroy(self)
+        except Exception:
+            pass
+
+
+@dataclasses.dataclass
+class SolveInfo:
+    status: int
+    iters: int
+    cycles: int
+    rel_resid: float
+    energy_kcal: float
+    rel_resid_fp64: float
+    refine_steps: int
+
+
+def pb_create(centroids, normals, areas, charges, eps1: float, eps2: float, kappa: float, stream=None) -> Context:
+    keep = []
+    n = int(np.prod(np.shape(areas)))
+    q = charges if charges is not None else np.zeros((0, 4))
+    nc = int(np.prod(np.shape(q))) // 4
+    out = ctypes.c_void_p()
+    st = lib().pb_create(_ptr_f64(centroids, 3 * n, "centroids", keep), _ptr_f64(normals, 3 * n, "normals", keep),
+                         _ptr_f64(areas, n, "areas", keep), n,
+                         _ptr_f64(q, 4 * nc, "charges", keep) if nc > 0 else None, nc,
+                         float(eps1), float(eps2), float(kappa), _stream_ptr(stream), ctypes.byref(out))
+    _check(st)
+    return Context(out.value, n, nc)
+
+
+def pb_set_charges(ctx: Context, charges) -> None:
+    keep = []
+    nc = int(np.prod(np.shape(charges))) // 4
+    _check(lib().pb_set_charges(ctx.handle, _ptr_f64(charges, 4 * nc, "charges", keep) if nc > 0 else None, nc), ctx)
+    ctx.nc = nc
+
+
+def pb_source(ctx: Context, b, prec="fp64") -> None:
+    _check(lib().pb_source(ctx.handle, _device_vec(b, 2 * ctx.n, "b"), PRECISIONS[prec]), ctx)
+
+
+def pb_matvec(ctx: Context, u, y, prec="fp32pair") -> None:
+    _check(lib().pb_matvec(ctx.handle, _device_vec(u, 2 * ctx.n, "u"), _device_vec(y, 2 * ctx.n, "y"),
+                           PRECISIONS[prec]), ctx)
+
+
+def pb_solve(ctx: Context, restart: int = 10, tol: float = 1e-4, maxit: int = 1000, prec="fp32pair",
+             refine: int = 0, x0=None, x_out=None, raise_on_noconv: bool = True) -> SolveInfo:
+    o = _Opts(int(restart), float(tol), int(maxit), PRECISIONS[prec], int(refine))
+    info = _Info()
+    x0p = _device_vec(x0, 2 * ctx.n, "x0") if x0 is not None else None
+    xop = _device_vec(x_out, 2 * ctx.n, "x_out") if x_out is not None else None
+    st = lib().pb_solve(ctx.handle, ctypes.byref(o), x0p, xop, ctypes.byref(info))
+    if st != PB_OK and not (st == PB_ERR_NOCONV and not raise_on_noconv):
+        _check(st, ctx)
+    return SolveInfo(st, info.iters, info.cycles, info.rel_resid, info.energy_kcal, info.rel_resid_fp64,
+                     info.refine_steps)
+
+
+def pb_energy(ctx: Context) -> float:
+    e = ctypes.c_double()
+    _check(lib().pb_energy(ctx.handle, ctypes.byref(e)), ctx)
+    return e.value
+
+
+def pb_energy_of(ctx: Context, u, prec="fp64") -> float:
+    e = ctypes.c_double()
+    _check(lib().pb_energy_of(ctx.handle, _device_vec(u, 2 * ctx.n, "u"), PRECISIONS[prec], ctypes.byref(e)), ctx)
+    return e.value
+
+
+def pb_get_info(ctx: Context) -> dict:
+    i = _CtxInfo()
+    _check(lib().pb_get_info(ctx.handle, ctypes.byref(i)), ctx)
+    return {"n": i.n, "nc": i.nc, "eps1": i.eps1, "eps2": i.eps2, "kappa": i.kappa, "center": list(i.center),
+            "gauss_min": i.gauss_min, "gauss_max": i.gauss_max, "device_bytes": i.device_bytes}
+
+
+def pb_destroy(ctx: Context) -> None:
+    if ctx is not None and ctx.handle:
+        h, ctx.handle = ctx.handle, None
+        lib().pb_destroy(h)

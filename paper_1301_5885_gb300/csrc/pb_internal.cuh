@@ -1,0 +1,170 @@
+// pb_internal.cuh -- shared declarations of the CUDA library behind include/pb.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pb.h"
+
+namespace pb {
+
+// e_c^2 / (4 pi eps_0 * 1 Angstrom) in kcal/mol (the energy unit of Eq. (14)).
+constexpr double kCoulombKcal = 332.0636;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kInv4Pi = 1.0 / (4.0 * kPi);
+
+constexpr int kMaxRestart = 64;       // largest GMRES restart length supported
+
+// One point charge (centred position and charge in e_c), 32-byte aligned so a
+// warp loads it with two 16-byte transactions per lane.
+struct alignas(32) Charge4 {
+    double x, y, z, q;
+};
+
+// ---- matvec tiling ---------------------------------------------------------
+// FP32-pair kernel: 128 threads x 4 targets = 512 targets per target tile,
+// 256 sources per shared-memory source tile.
+constexpr int kF32Threads = 128;
+constexpr int kF32TargetsPerThread = 4;
+constexpr int kF32TargetTile = kF32Threads * kF32TargetsPerThread;
+constexpr int kF32SourceTile = 256;
+// FP64 kernel: 128 threads x 1 target, 128 sources per source tile.
+constexpr int kF64Threads = 128;
+constexpr int kF64TargetTile = kF64Threads;
+constexpr int kF64SourceTile = 128;
+
+// Stream-K style split of the (target tile x source tile) iteration space over
+// a fixed number of persistent CTAs.  CTA c owns the flattened tile-pair range
+// [c*W/G, (c+1)*W/G); target tile a is covered by the contiguous CTAs
+// cta_of(a*S) .. cta_of(a*S + S - 1).
+struct StreamKPlan {
+    int64_t target_tiles;   // T
+    int64_t source_tiles;   // S
+    int64_t work;           // W = T * S
+    int64_t ctas;           // G, 1 <= G <= W
+    int64_t max_segments;   // largest number of CTAs covering one target tile
+};
+
+__host__ __device__ inline int64_t sk_begin(int64_t c, int64_t W, int64_t G) { return (c * W) / G; }
+// the CTA whose range contains tile-pair p: ceil((p+1) G / W) - 1
+__host__ __device__ inline int64_t sk_cta_of(int64_t p, int64_t W, int64_t G) {
+    return ((p + 1) * G + W - 1) / W - 1;
+}
+
+StreamKPlan make_plan(int64_t n, int target_tile, int source_tile, int64_t ctas_wanted);
+
+// ---- GMRES device state ----------------------------------------------------
+struct GmresState {
+    double H[(kMaxRestart + 1) * kMaxRestart];   // column-major, ld = kMaxRestart + 1
+    double cs[kMaxRestart], sn[kMaxRestart];
+    double g[kMaxRestart + 1];
+    double h1[kMaxRestart + 1];   // first Gram-Schmidt pass coefficients
+    double h2[kMaxRestart + 1];   // second pass
+    double y[kMaxRestart];
+    double bnorm;
+    double beta;                  // ||r0|| of the current cycle
+    double hnext;                 // H[k+1][k] of the current step
+    double rel_resid;             // last true relative residual
+    double est_resid;             // Givens estimate |g[k+1]| / bnorm
+    double tol;
+    int m;                        // restart length
+    int maxit;
+    int k;                        // Arnoldi columns completed in this cycle
+    int iters;                    // total Arnoldi steps
+    int cycles;
+    int cycle_done;               // 1: remaining steps of this cycle are skipped
+    int done;                     // 1: converged or stopped; every kernel is skipped
+    int skip;                     // done || cycle_done (read by the matvec kernels)
+    int converged;
+    int status;                   // pb_status
+    int x_is_zero;                // the current x is exactly zero (skip A x)
+};
+
+}  // namespace pb
+
+// ---- context -----------------------------------------------------------------
+struct pb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t N = 0, Nc = 0;
+    double eps1 = 1, eps2 = 1, eps = 1, kappa = 0;
+    double center[3] = {0, 0, 0};
+    double gauss_min = 0, gauss_max = 0;
+    int num_sms = 0;
+
+    // geometry, shifted by center
+    double *g64 = nullptr;       // SoA 7N: x | y | z | nx | ny | nz | W
+    float4 *pos32 = nullptr;     // {x, y, z, W / (4 pi)}
+    float4 *nrm32 = nullptr;     // {nx, ny, nz, 0}
+    pb::Charge4 *charges = nullptr;  // {x, y, z, Q}, Nc entries (capacity nc_cap)
+    int64_t nc_cap = 0;
+
+    // vectors (2N each)
+    double *b = nullptr;         // right-hand side for the current charges
+    double *x = nullptr;         // last solution
+    bool b_valid = false, x_valid = false;
+
+    // matvec scratch: per (target tile, segment) partial row sums, and one
+    // arrival counter per target tile (left at zero between launches)
+    pb::StreamKPlan plan32{}, plan64{};
+    double *partials = nullptr;
+    int64_t partials_len = 0;
+    unsigned int *tile_counters = nullptr;
+    int64_t counters_len = 0;
+
+    // reductions
+    double *red = nullptr;       // block partials
+    int64_t red_len = 0;
+    unsigned int *red_counter = nullptr;
+    double *scalar = nullptr;    // device scalars (energy, norms)
+    double *host_scalar = nullptr;   // pinned
+
+    // GMRES workspace
+    int gm_m = 0;
+    double *V = nullptr;         // (m+1) x 2N
+    double *w = nullptr;         // 2N
+    double *r = nullptr;         // 2N
+    double *d = nullptr;         // 2N (refinement correction)
+    double *rres = nullptr;      // 2N (refinement residual b - A_fp64 x)
+    pb::GmresState *st = nullptr;
+    pb::GmresState *st_host = nullptr;   // pinned
+
+    int64_t device_bytes = 0;
+    char last_error[512] = {0};
+};
+
+namespace pb {
+
+// error helpers (pb_api.cu)
+pb_status set_error(pb_ctx *ctx, pb_status s, const char *fmt, ...);
+pb_status cuda_error(pb_ctx *ctx, cudaError_t e, const char *what);
+void count_launch();
+#define PB_LAUNCHED() ::pb::count_launch()
+
+// allocation on the context's stream (stream-ordered pool)
+pb_status ctx_alloc(pb_ctx *ctx, void **p, size_t bytes, const char *what);
+void ctx_free(pb_ctx *ctx, void *p);
+
+// geom.cu
+pb_status geometry_prepare(pb_ctx *ctx, const double *c_dev, const double *n_dev, const double *a_dev);
+pb_status charges_prepare(pb_ctx *ctx, const double *q_dev, int64_t nc);
+pb_status gauss_check(pb_ctx *ctx, double *gmin, double *gmax);
+
+// matvec.cu
+pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision prec, const int *skip_flag);
+int matvec_occupancy(pb_precision prec);
+
+// source_energy.cu
+pb_status source_launch(pb_ctx *ctx, double *b, pb_precision prec);
+pb_status energy_launch(pb_ctx *ctx, const double *u, pb_precision prec, double *dev_out);
+
+// gmres.cu
+pb_status gmres_solve(pb_ctx *ctx, const pb_solve_opts *o, const double *rhs, double *x, bool x_is_zero,
+                      int *iters, int *cycles, double *rel_resid);
+pb_status norm2_launch(pb_ctx *ctx, const double *v, int64_t n, double *dev_out);
+
+// reduction sizing shared by the kernels
+constexpr int kRedThreads = 256;
+int red_blocks(pb_ctx *ctx, int64_t n);
+
+}  // namespace pb

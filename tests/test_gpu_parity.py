@@ -1,0 +1,271 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the FP64 oracle.
+
+Tolerances (see the design doc for the derivation):
+  FP64 path      matvec rel-L2 <= 1e-10, elementwise <= 1e-9 * max|y|;
+                 source rel-L2 <= 1e-12; energy rel <= 1e-10.
+  FP32-pair path matvec rel-L2 <= 2e-5; source rel-L2 <= 2e-6;
+                 solvation energy of a solve rel <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import pb_inputs as pi
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import importlib
+    importlib.import_module("paper_1301_5885_gb300.build").build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _pb():
+    import paper_1301_5885_gb300 as pb
+    return pb
+
+
+def _ctx(surface, charges=None, eps1=1.0, eps2=80.0, kappa=0.1257):
+    pb = _pb()
+    return pb.pb_create(surface.centroids, surface.normals, surface.areas, charges, eps1, eps2, kappa,
+                        stream=torch.cuda.current_stream())
+
+
+def _u(n, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.normal(size=2 * n)
+
+
+def _gpu_matvec(ctx, u, prec):
+    pb = _pb()
+    ud = torch.tensor(u, dtype=torch.float64, device="cuda")
+    y = torch.full_like(ud, float("nan"))
+    pb.pb_matvec(ctx, ud, y, prec)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def _surfaces():
+    big = pi.icosphere(3.0, 4)
+    out = [("ico0", pi.icosphere(2.0, 0)), ("ico2", pi.icosphere(2.0, 2)), ("ico3", pi.icosphere(5.0, 3)),
+           ("ico4", big)]
+    # ragged sizes: subsets that are not multiples of any tile size
+    for n in (1, 2, 3, 33, 513, 777, 4099):
+        out.append((f"sub{n}", big.subset(np.arange(n) * (big.n // n))))
+    out.append(("solute", pi.protein_like(n_atoms=8, seed=1, target_triangles=None, spacing=1.6).surface))
+    return out
+
+
+SURFACES = _surfaces()
+
+
+@pytest.mark.parametrize("name,surf", SURFACES, ids=[s[0] for s in SURFACES])
+@pytest.mark.parametrize("kappa", [0.1257, 0.0])
+def test_matvec_fp64_matches_oracle(name, surf, kappa):
+    u = _u(surf.n, 1)
+    with _ctx(surf, kappa=kappa) as ctx:
+        y = _gpu_matvec(ctx, u, "fp64")
+    ref = oracle.matvec(surf, 80.0, kappa, u)
+    assert np.all(np.isfinite(y))
+    assert np.linalg.norm(y - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert np.max(np.abs(y - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("name,surf", SURFACES, ids=[s[0] for s in SURFACES])
+@pytest.mark.parametrize("kappa", [0.1257, 0.0])
+def test_matvec_fp32pair_matches_oracle(name, surf, kappa):
+    u = _u(surf.n, 2)
+    with _ctx(surf, kappa=kappa) as ctx:
+        y = _gpu_matvec(ctx, u, "fp32pair")
+    ref = oracle.matvec(surf, 80.0, kappa, u)
+    assert np.all(np.isfinite(y))
+    assert np.linalg.norm(y - ref) <= 2e-5 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32pair"])
+def test_matvec_is_identity_without_jump_or_salt(prec):
+    surf = pi.icosphere(2.0, 3)
+    u = _u(surf.n, 3)
+    with _ctx(surf, eps1=2.0, eps2=2.0, kappa=0.0) as ctx:
+        y = _gpu_matvec(ctx, u, prec)
+    assert np.array_equal(y, u)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32pair"])
+def test_single_element_has_only_the_diagonal(prec):
+    surf = pi.icosphere(2.0, 1).subset([5])
+    u = np.array([0.7, -1.3])
+    with _ctx(surf) as ctx:
+        y = _gpu_matvec(ctx, u, prec)
+    assert y[0] == 0.5 * (1 + 80.0) * 0.7
+    assert y[1] == 0.5 * (1 + 1 / 80.0) * -1.3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32pair"])
+def test_duplicate_centroids_are_dropped_like_the_self_term(prec):
+    base = pi.icosphere(2.0, 2)
+    idx = np.concatenate([np.arange(base.n), [7, 7, 100]])
+    surf = base.subset(idx)
+    u = _u(surf.n, 4)
+    with _ctx(surf) as ctx:
+        y = _gpu_matvec(ctx, u, prec)
+    ref = oracle.matvec(surf, 80.0, 0.1257, u)
+    tol = 1e-10 if prec == "fp64" else 2e-5
+    assert np.all(np.isfinite(y))
+    assert np.linalg.norm(y - ref) <= tol * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32pair"])
+def test_matvec_is_deterministic(prec):
+    surf = pi.icosphere(4.0, 4)
+    u = _u(surf.n, 5)
+    with _ctx(surf) as ctx:
+        y1 = _gpu_matvec(ctx, u, prec)
+        y2 = _gpu_matvec(ctx, u, prec)
+    assert np.array_equal(y1, y2)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32pair", 2e-6)])
+def test_source_matches_oracle(prec, tol):
+    pb = _pb()
+    p = pi.kirkwood_sphere_multi(level=4, radius=10.0, n_charges=300, seed=3)
+    with _ctx(p.surface, p.charges) as ctx:
+        b = torch.empty(2 * p.n, dtype=torch.float64, device="cuda")
+        pb.pb_source(ctx, b, prec)
+        torch.cuda.synchronize()
+        b = b.cpu().numpy()
+    ref = oracle.source(p.surface, p.charges, 1.0)
+    assert np.linalg.norm(b - ref) <= tol * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32pair", 1e-5)])
+def test_energy_of_matches_oracle(prec, tol):
+    pb = _pb()
+    p = pi.kirkwood_sphere_multi(level=3, radius=8.0, n_charges=280, seed=6)
+    u = _u(p.n, 7) * 1e-2
+    with _ctx(p.surface, p.charges) as ctx:
+        e = pb.pb_energy_of(ctx, torch.tensor(u, device="cuda"), prec)
+    ref = oracle.reaction_energy(p.surface, p.charges, 80.0, 0.1257, u)
+    assert e == pytest.approx(ref, rel=tol)
+
+
+def _problems():
+    return [pi.kirkwood_sphere_multi(level=3, radius=6.0, n_charges=7, seed=8),
+            pi.kirkwood_sphere_single(level=3),
+            pi.protein_like(n_atoms=10, seed=4, target_triangles=None, spacing=1.7)]
+
+
+@pytest.mark.parametrize("k", range(3))
+def test_solve_fp64_matches_oracle(k):
+    pb = _pb()
+    p = _problems()[k]
+    ref = oracle.solve(p.surface, p.charges, p.eps1, p.eps2, p.kappa, tol=1e-12, maxit=2000)
+    with _ctx(p.surface, p.charges, p.eps1, p.eps2, p.kappa) as ctx:
+        x = torch.empty(2 * p.n, dtype=torch.float64, device="cuda")
+        info = pb.pb_solve(ctx, restart=10, tol=1e-12, maxit=2000, prec="fp64", x_out=x)
+        assert pb.pb_energy(ctx) == info.energy_kcal
+    assert info.status == pb.PB_OK and info.rel_resid <= 1e-12
+    u = x.cpu().numpy()
+    assert np.linalg.norm(u - ref["u"]) <= 1e-9 * np.linalg.norm(ref["u"])
+    assert info.energy_kcal == pytest.approx(ref["energy"], rel=1e-10)
+
+
+@pytest.mark.parametrize("k", range(3))
+def test_solve_fp32pair_energy_within_1e5(k):
+    pb = _pb()
+    p = _problems()[k]
+    ref = oracle.solve(p.surface, p.charges, p.eps1, p.eps2, p.kappa, tol=1e-12, maxit=2000)
+    with _ctx(p.surface, p.charges, p.eps1, p.eps2, p.kappa) as ctx:
+        info = pb.pb_solve(ctx, restart=10, tol=1e-7, maxit=2000, prec="fp32pair")
+    assert info.status == pb.PB_OK
+    assert info.energy_kcal == pytest.approx(ref["energy"], rel=1e-5)
+
+
+def test_refinement_reaches_fp64_residual():
+    pb = _pb()
+    p = _problems()[0]
+    with _ctx(p.surface, p.charges, p.eps1, p.eps2, p.kappa) as ctx:
+        plain = pb.pb_solve(ctx, restart=10, tol=1e-9, maxit=2000, prec="fp32pair", raise_on_noconv=False)
+        ref = pb.pb_solve(ctx, restart=10, tol=1e-12, maxit=2000, prec="fp64")
+        refined = pb.pb_solve(ctx, restart=10, tol=1e-9, maxit=2000, prec="fp32pair", refine=2)
+    assert refined.refine_steps == 2
+    assert refined.rel_resid_fp64 <= 1e-8
+    assert abs(refined.energy_kcal - ref.energy_kcal) <= abs(plain.energy_kcal - ref.energy_kcal) + 1e-12 * abs(ref.energy_kcal)
+    assert refined.energy_kcal == pytest.approx(ref.energy_kcal, rel=1e-8)
+
+
+def test_warm_start_takes_fewer_iterations():
+    pb = _pb()
+    p = _problems()[0]
+    with _ctx(p.surface, p.charges) as ctx:
+        x = torch.empty(2 * p.n, dtype=torch.float64, device="cuda")
+        cold = pb.pb_solve(ctx, tol=1e-8, prec="fp64", x_out=x)
+        warm = pb.pb_solve(ctx, tol=1e-8, prec="fp64", x0=x)
+    assert warm.iters < cold.iters
+    assert warm.energy_kcal == pytest.approx(cold.energy_kcal, rel=1e-7)
+
+
+def test_no_charges_gives_zero_solution_and_energy():
+    pb = _pb()
+    s = pi.icosphere(2.0, 2)
+    with _ctx(s) as ctx:
+        x = torch.full((2 * s.n,), 5.0, dtype=torch.float64, device="cuda")
+        info = pb.pb_solve(ctx, prec="fp32pair", x_out=x)
+        assert info.energy_kcal == 0.0 and info.iters == 0
+        assert torch.count_nonzero(x).item() == 0
+
+
+def test_set_charges_changes_the_right_hand_side():
+    pb = _pb()
+    p = pi.kirkwood_sphere_multi(level=3, radius=6.0, n_charges=5, seed=9)
+    q2 = p.charges.copy()
+    q2[:, 3] *= -2.0
+    with _ctx(p.surface, p.charges) as ctx:
+        e1 = pb.pb_solve(ctx, tol=1e-10, prec="fp64").energy_kcal
+        pb.pb_set_charges(ctx, q2)
+        e2 = pb.pb_solve(ctx, tol=1e-10, prec="fp64").energy_kcal
+    assert e2 == pytest.approx(4.0 * e1, rel=1e-8)     # E is quadratic in the charges
+
+
+def test_bad_meshes_are_rejected():
+    pb = _pb()
+    s = pi.icosphere(2.0, 2)
+    q = np.array([[0.0, 0.0, 0.0, 1.0]])
+    bad = pi.Surface(s.centroids.copy(), s.normals.copy(), s.areas.copy())
+    bad.areas[3] = 0.0
+    with pytest.raises(pb.PBError) as ei:
+        _ctx(bad, q)
+    assert ei.value.status == pb.PB_ERR_BADMESH
+    bad = pi.Surface(s.centroids.copy(), s.normals.copy() * 1.1, s.areas.copy())
+    with pytest.raises(pb.PBError) as ei:
+        _ctx(bad, q)
+    assert ei.value.status == pb.PB_ERR_BADMESH
+    inward = pi.Surface(s.centroids.copy(), -s.normals, s.areas.copy())
+    with pytest.raises(pb.PBError) as ei:
+        _ctx(inward, q)
+    assert ei.value.status == pb.PB_ERR_BADMESH
+    with pytest.raises(pb.PBError) as ei:
+        _ctx(s, np.array([[5.0, 0.0, 0.0, 1.0]]))      # charge outside the surface
+    assert ei.value.status == pb.PB_ERR_BADMESH
+
+
+def test_geometry_info_and_translation_invariance():
+    pb = _pb()
+    p = pi.kirkwood_sphere_multi(level=3, radius=6.0, n_charges=5, seed=10)
+    shift = np.array([1000.0, -250.0, 40.0])
+    moved = p.surface.transformed(shift=shift)
+    q = p.charges.copy()
+    q[:, :3] += shift
+    with _ctx(p.surface, p.charges) as a, _ctx(moved, q) as b:
+        ia, ib = pb.pb_get_info(a), pb.pb_get_info(b)
+        assert np.allclose(np.array(ib["center"]) - np.array(ia["center"]), shift)
+        assert -1.05 < ia["gauss_min"] <= ia["gauss_max"] < -0.95
+        ea = pb.pb_solve(a, tol=1e-7, prec="fp32pair").energy_kcal
+        eb = pb.pb_solve(b, tol=1e-7, prec="fp32pair").energy_kcal
+    assert eb == pytest.approx(ea, rel=1e-5)       # FP32 coordinates are centred first
