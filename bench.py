@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the direct-sum boundary-integral PB solve on one or more GPUs.
+
+One step = the whole hot path for one molecule: pb_create from device-resident
+geometry (validation, centring, FP32/FP64 packing, orientation check), the
+source term, restarted GMRES whose products with A are the FP32-pair
+direct-sum matvec (FP64 accumulation, FP64 Krylov arithmetic), and the FP64
+solvation-energy reduction; then the context is freed.
+
+The headline value is the matvec pair rate of the whole step: (products with A
+the device evaluated) x N(N-1) pairs / step time, in Gpairs/s.  The line also
+reports solves/s, p50/p99 step latency, the relative energy error against the
+stored FP64 oracle solution, the roofline fraction of the matvec kernel, an
+end-to-end figure through the C ABI from pinned host buffers, and the oracle
+timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torchrun; every rank solves its own copy (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "matvec Gpairs/s; PB solves/s + p50/p99 latency at ≤1e-5 rel. energy error"
+UNIT = "Gpairs/s"
+
+# Roofline of the FP32-pair matvec (ALU bound, no tensor-core contraction).
+# The algorithmic work per pair is 41 FP32 add/mul/fma operations plus 2 MUFU
+# operations (rsqrt, ex2).  The FP32 pipe retires 128 lanes per clock per SM,
+# MUFU 16, so the FP32 pipe binds: peak pairs/s = SMs x 128 x f_max / 41
+# (the MUFU ceiling, SMs x 16 x f_max / 2, is 2.6x higher).
+FP32_OPS_PER_PAIR = 41
+SMS = 152
+SM_MAX_MHZ = 2070.0
+PEAK_GPAIRS = SMS * 128 * SM_MAX_MHZ * 1e6 / FP32_OPS_PER_PAIR / 1e9
+# dram__bytes_read.sum + dram__bytes_write.sum of one matvec_f32_kernel launch
+# on the 81,920-triangle sphere, from the ncu capture summarised in
+# profiles/matvec_f32_kernel_sphere2_full.md; None once the kernel has changed.
+MATVEC_TRAFFIC_BYTES = {("matvec_f32_kernel", "sphere2"): 3988992}
+
+WORKLOADS = {
+    "sphere2": "Kirkwood sphere R=20 A, icosphere level 6 (81,920 triangles), 20 charges in 0.8R, "
+               "eps 1/80, kappa 0.1257",
+    "sphere1": "Born sphere R=2 A, icosphere level 4 (5,120 triangles), one central charge, eps 1/80, kappa 0.1257",
+    "protein300k": "protein-like 2,000-atom chain, probe-inflated Gaussian isosurface (~300k triangles)",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sphere2")
+    ap.add_argument("--prec", choices=["fp32pair", "fp64"], default="fp32pair")
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--restart", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def golden_energy(name):
+    path = os.path.join(ROOT, "tests", "golden", "oracle_energies.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    return d.get(name, {}).get("energy_kcal")
+
+
+# --- clocks --------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(", ") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        if self.uuid:
+            mine = [r for r in rows if r and self.uuid in r[0]]
+            rows = mine or rows
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --- the reference arm: the FP64 oracle on the host cores -----------------------
+def oracle_rate(prob, seconds: float, seed: int = 0):
+    """Time the oracle's direct-sum rows (Eqs. (12)-(13)) on a row sample sized to
+    about ``seconds`` of host work.  Returns (Gpairs/s, rows, elapsed, threads)."""
+    import numpy as np
+    import oracle
+    s = prob.surface
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u = rng.normal(size=2 * prob.n)
+    eps = prob.eps2 / prob.eps1
+    probe = min(prob.n, 32)
+    t = time.perf_counter()
+    oracle.matvec_rows(s, eps, prob.kappa, u, rng.choice(prob.n, probe, replace=False))
+    dt = max(time.perf_counter() - t, 1e-6)
+    rows = int(max(1, min(prob.n, probe * seconds / dt)))
+    idx = rng.choice(prob.n, rows, replace=False)
+    t = time.perf_counter()
+    oracle.matvec_rows(s, eps, prob.kappa, u, idx)
+    el = time.perf_counter() - t
+    return rows * (prob.n - 1) / el / 1e9, rows, el, oracle.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import pb_inputs
+    prob = pb_inputs.by_name(args.workload)
+    budget = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_rate(prob, budget * 0.25)
+    rates, times, rows_total = [], [], 0
+    for k in range(args.steps):
+        r, rows, el, threads = oracle_rate(prob, budget, seed=k + 1)
+        rates.append(r)
+        times.append(el)
+        rows_total += rows
+    total_pairs = rows_total * (prob.n - 1)
+    value = total_pairs / sum(times) / 1e9
+    sample = (f"{rows_total // max(1, args.steps)} sampled rows (both row blocks) of the N={prob.n} direct-sum "
+              f"matvec per step, FP64 oracle, {threads} OpenMP threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args, prob),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(args, prob):
+    return {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_triangles": prob.n,
+            "n_charges": prob.nc, "precision": args.prec, "gmres_restart": args.restart, "gmres_tol": args.tol,
+            "l2": "flushed between steps (256 MiB write)"}
+
+
+def reduce_over_ranks(total_ms: float, pairs: float, solves: float, device, dist=None):
+    """Whole-job totals: the slowest rank's time (max) and the units of all ranks
+    (sum).  ``dist`` is torch.distributed (or None for one process)."""
+    import torch
+    t = torch.tensor([float(total_ms), float(pairs), float(solves)], dtype=torch.float64, device=device)
+    if dist is None:
+        return t[0].item(), t[1].item(), t[2].item()
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx[0].item(), sm[1].item(), sm[2].item()
+
+
+# --- our arm --------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1301_5885_gb300 as pb
+    import pb_inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    prob = pb_inputs.by_name(args.workload)
+    s = prob.surface
+    n = prob.n
+    pairs_per_mv = n * (n - 1)
+    # inputs resident in HBM before the timed region
+    c_d = torch.tensor(s.centroids, device=dev)
+    n_d = torch.tensor(s.normals, device=dev)
+    a_d = torch.tensor(s.areas, device=dev)
+    q_d = torch.tensor(prob.charges, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(c, nr, a, q, profile=False):
+        ctx = pb.pb_create(c, nr, a, q, prob.eps1, prob.eps2, prob.kappa, stream=stream)
+        try:
+            if profile:
+                pb.pb_profile_enable(ctx, True)
+            info = pb.pb_solve(ctx, restart=args.restart, tol=args.tol, maxit=2000, prec=args.prec)
+            prof = pb.pb_profile_read(ctx) if profile else None
+        finally:
+            pb.pb_destroy(ctx)
+        return info, prof
+
+    for _ in range(args.warmup):
+        step(c_d, n_d, a_d, q_d)
+    torch.cuda.synchronize()
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = pb.pb_kernel_launches()
+    evs = []
+    infos, profs = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info, prof = step(c_d, n_d, a_d, q_d, profile=True)
+        e1.record(stream)
+        evs.append((e0, e1))
+        infos.append(info)
+        profs.append(prof)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = pb.pb_kernel_launches() - launches0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    matvecs = sum(i.matvecs for i in infos)
+    my_pairs = matvecs * pairs_per_mv
+    total_ms_max, all_pairs, all_solves = reduce_over_ranks(total_ms, my_pairs, args.steps, dev, dist)
+    value = all_pairs / (total_ms_max * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the FP32-pair (or FP64) matvec
+    mv_ms = sum(p["matvec_ms"] for p in profs)
+    mv_n = sum(p["evaluated"] for p in profs)
+    avg_ms = mv_ms / max(1, mv_n)
+    achieved = pairs_per_mv / (avg_ms * 1e-3) / 1e9
+    mv_share = mv_ms / total_ms
+
+    result = None
+    kname = "matvec_f32_kernel" if args.prec == "fp32pair" else "matvec_f64_kernel"
+    if rank == 0:
+        ref_e = golden_energy(args.workload)
+        energies = [i.energy_kcal for i in infos]
+        rel_err = max(abs(e - ref_e) / abs(ref_e) for e in energies) if ref_e else None
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 pairs, f64 accumulation" if args.prec == "fp32pair" else "f64",
+                "data": "synthetic", "config": config_dict(args, prob),
+                "solves_per_s": all_solves / (total_ms_max * 1e-3),
+                "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+                "energy_kcal": energies[-1], "oracle_energy_kcal": ref_e, "rel_energy_err": rel_err,
+                "gmres": {"iters": infos[-1].iters, "matvecs": infos[-1].matvecs,
+                          "rel_resid": infos[-1].rel_resid},
+                "roofline": {"kernel": kname,
+                             "bound": "alu", "achieved": achieved, "peak": PEAK_GPAIRS, "unit": UNIT,
+                             "frac": achieved / PEAK_GPAIRS,
+                             "traffic": MATVEC_TRAFFIC_BYTES.get((kname, args.workload)),
+                             "peak_basis": f"FP32 pipe: {SMS} SMs x 128 lanes x {SM_MAX_MHZ:.0f} MHz / "
+                                           f"{FP32_OPS_PER_PAIR} FP32 ops per pair (derived from unit counts "
+                                           "and the maximum SM clock; not a measured peak)",
+                             "avg_launch_ms": avg_ms, "launches": mv_n, "share_of_step": mv_share},
+                "gpu_launches": launches, "clocks": clocks}
+        result = line
+    if dist:
+        dist.barrier()
+
+    if rank == 0 and not args.no_e2e:
+        # end to end through the C ABI from pinned host buffers: H2D of the
+        # inputs and D2H of the energy inside every timed step
+        c_h = torch.tensor(s.centroids).pin_memory()
+        n_h = torch.tensor(s.normals).pin_memory()
+        a_h = torch.tensor(s.areas).pin_memory()
+        q_h = torch.tensor(prob.charges).pin_memory()
+        step(c_h, n_h, a_h, q_h)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        mvs = 0
+        for _ in range(args.steps):
+            info, _ = step(c_h, n_h, a_h, q_h)
+            mvs += info.matvecs
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        h2d = (c_h.numel() + n_h.numel() + a_h.numel() + q_h.numel()) * 8
+        result["e2e"] = {"value": mvs * pairs_per_mv / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                         "d2h_bytes_per_step": 8, "ms_per_step": 1e3 * el / args.steps,
+                         "solves_per_s": args.steps / el}
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, rows, el, threads = oracle_rate(prob, args.cpu_seconds)
+        result["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                  "sample": f"{rows} sampled rows (both row blocks) of the N={n} direct-sum matvec, "
+                                            f"FP64 oracle, {threads} OpenMP threads, {el:.1f} s"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

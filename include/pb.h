@@ -76,6 +76,8 @@ typedef struct {
     double energy_kcal;   /* E_sol of Eq. (14) for the solution, FP64 reduction */
     double rel_resid_fp64;/* ||b - A_fp64 x|| / ||b|| when refine > 0, else -1 */
     int refine_steps;     /* refinement steps taken */
+    int64_t matvecs;      /* products with A the device actually evaluated
+                             (Arnoldi steps, true residuals, refinement) */
 } pb_solve_info;
 
 typedef struct {
@@ -142,6 +144,17 @@ const char *pb_last_error(const pb_ctx *ctx);
 
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t pb_kernel_launches(void);
+
+/* Kernel timing for measurement (not part of the method).  While enabled,
+ * every matrix-vector product launched by this context is bracketed by CUDA
+ * events recorded on the context's stream.  pb_profile_read waits for the
+ * stream, then returns the summed event time of those launches in ms, the
+ * number of timed launches, and the number of products the device actually
+ * evaluated (launches whose GMRES state said "skip" return at once and are
+ * timed but not counted there).  reset != 0 clears the totals. */
+pb_status pb_profile_enable(pb_ctx *ctx, int enable);
+pb_status pb_profile_read(pb_ctx *ctx, double *matvec_ms, int64_t *timed_launches, int64_t *evaluated,
+                          int reset);
 
 #ifdef __cplusplus
 }

@@ -34,7 +34,7 @@ class _Opts(ctypes.Structure):
 class _Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("rel_resid", ctypes.c_double),
                 ("energy_kcal", ctypes.c_double), ("rel_resid_fp64", ctypes.c_double),
-                ("refine_steps", ctypes.c_int)]
+                ("refine_steps", ctypes.c_int), ("matvecs", ctypes.c_int64)]
 
 
 class _CtxInfo(ctypes.Structure):
@@ -58,6 +58,8 @@ SIGNATURES = {
     "pb_status_string": (ctypes.c_char_p, [_I]),
     "pb_last_error": (ctypes.c_char_p, [_VP]),
     "pb_kernel_launches": (ctypes.c_uint64, []),
+    "pb_profile_enable": (_I, [_VP, _I]),
+    "pb_profile_read": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), ctypes.POINTER(_I64), _I]),
 }
 
 _LIB = None
@@ -179,6 +181,7 @@ class SolveInfo:
     energy_kcal: float
     rel_resid_fp64: float
     refine_steps: int
+    matvecs: int
 
 
 def pb_create(centroids, normals, areas, charges, eps1: float, eps2: float, kappa: float, stream=None) -> Context:
@@ -221,7 +224,7 @@ def pb_solve(ctx: Context, restart: int = 10, tol: float = 1e-4, maxit: int = 10
     if st != PB_OK and not (st == PB_ERR_NOCONV and not raise_on_noconv):
         _check(st, ctx)
     return SolveInfo(st, info.iters, info.cycles, info.rel_resid, info.energy_kcal, info.rel_resid_fp64,
-                     info.refine_steps)
+                     info.refine_steps, info.matvecs)
 
 
 def pb_energy(ctx: Context) -> float:
@@ -241,6 +244,17 @@ def pb_get_info(ctx: Context) -> dict:
     _check(lib().pb_get_info(ctx.handle, ctypes.byref(i)), ctx)
     return {"n": i.n, "nc": i.nc, "eps1": i.eps1, "eps2": i.eps2, "kappa": i.kappa, "center": list(i.center),
             "gauss_min": i.gauss_min, "gauss_max": i.gauss_max, "device_bytes": i.device_bytes}
+
+
+def pb_profile_enable(ctx: Context, enable: bool = True) -> None:
+    _check(lib().pb_profile_enable(ctx.handle, 1 if enable else 0), ctx)
+
+
+def pb_profile_read(ctx: Context, reset: bool = False) -> dict:
+    ms, timed, ev = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().pb_profile_read(ctx.handle, ctypes.byref(ms), ctypes.byref(timed), ctypes.byref(ev),
+                                 1 if reset else 0), ctx)
+    return {"matvec_ms": ms.value, "timed_launches": timed.value, "evaluated": ev.value}
 
 
 def pb_destroy(ctx: Context) -> None:

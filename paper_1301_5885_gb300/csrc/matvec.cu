@@ -127,9 +127,10 @@ __global__ void __launch_bounds__(kF32Threads)
 matvec_f32_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm,
                   const double *__restrict__ u, int64_t N, F32Params prm, StreamKPlan plan,
                   double *__restrict__ partials, unsigned int *__restrict__ counters,
-                  double *__restrict__ y, const int *__restrict__ skip) {
+                  double *__restrict__ y, const int *__restrict__ skip, unsigned long long *__restrict__ evaluated) {
     constexpr int BS = kF32Threads, T = kF32TargetsPerThread, TT = kF32TargetTile, TS = kF32SourceTile;
     if (skip != nullptr && *((volatile const int *)skip)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
     __shared__ float4 s_pos[TS];   // x, y, z, W dphi / (4 pi)
     __shared__ float4 s_nrm[TS];   // nx, ny, nz, W phi / (4 pi)
 
@@ -220,9 +221,10 @@ struct F64Params {
 __global__ void __launch_bounds__(kF64Threads)
 matvec_f64_kernel(const double *__restrict__ g64, const double *__restrict__ u, int64_t N, F64Params prm,
                   StreamKPlan plan, double *__restrict__ partials, unsigned int *__restrict__ counters,
-                  double *__restrict__ y, const int *__restrict__ skip) {
+                  double *__restrict__ y, const int *__restrict__ skip, unsigned long long *__restrict__ evaluated) {
     constexpr int BS = kF64Threads, TT = kF64TargetTile, TS = kF64SourceTile;
     if (skip != nullptr && *((volatile const int *)skip)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
     __shared__ double s_x[TS], s_y[TS], s_z[TS], s_nx[TS], s_ny[TS], s_nz[TS], s_wpsi[TS], s_wphi[TS];
     const double *X = g64, *Y = g64 + N, *Z = g64 + 2 * N;
     const double *NX = g64 + 3 * N, *NY = g64 + 4 * N, *NZ = g64 + 5 * N, *W = g64 + 6 * N;
@@ -290,6 +292,16 @@ matvec_f64_kernel(const double *__restrict__ g64, const double *__restrict__ u, 
 
 pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision prec, const int *skip_flag) {
     const double diag1 = 0.5 * (1.0 + ctx->eps), diag2 = 0.5 * (1.0 + 1.0 / ctx->eps);
+    if (prec != PB_FP32PAIR && prec != PB_FP64)
+        return set_error(ctx, PB_ERR_ARG, "pb_matvec: unknown precision %d", (int)prec);
+    const bool timed = ctx->prof_on;
+    if (timed) {
+        if (ctx->prof_used + 2 > (int)ctx->prof_ev.size()) {
+            pb_status fs = profile_flush(ctx);
+            if (fs != PB_OK) return fs;
+        }
+        cudaEventRecord(ctx->prof_ev[ctx->prof_used], ctx->stream);
+    }
     if (prec == PB_FP32PAIR) {
         F32Params prm;
         prm.eps = (float)ctx->eps;
@@ -300,16 +312,20 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         prm.diag2 = diag2;
         const StreamKPlan &pl = ctx->plan32;
         matvec_f32_kernel<<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(
-            ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag);
-    } else if (prec == PB_FP64) {
+            ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,
+            ctx->mv_count);
+    } else {
         F64Params prm{ctx->eps, 1.0 / ctx->eps, ctx->kappa, diag1, diag2};
         const StreamKPlan &pl = ctx->plan64;
         matvec_f64_kernel<<<(unsigned)pl.ctas, kF64Threads, 0, ctx->stream>>>(
-            ctx->g64, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag);
-    } else {
-        return set_error(ctx, PB_ERR_ARG, "pb_matvec: unknown precision %d", (int)prec);
+            ctx->g64, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag, ctx->mv_count);
     }
     PB_LAUNCHED();
+    if (timed) {
+        cudaEventRecord(ctx->prof_ev[ctx->prof_used + 1], ctx->stream);
+        ctx->prof_used += 2;
+        ctx->prof_launches += 1;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "matvec launch");
     return PB_OK;

@@ -49,6 +49,20 @@ void ctx_free(pb_ctx *ctx, void *p) {
     if (p) cudaFreeAsync(p, ctx->stream);
 }
 
+pb_status profile_flush(pb_ctx *ctx) {
+    if (ctx->prof_used == 0) return PB_OK;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "profile flush");
+    for (int i = 0; i + 1 < ctx->prof_used; i += 2) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, ctx->prof_ev[i], ctx->prof_ev[i + 1]);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "profile event");
+        ctx->prof_ms += ms;
+    }
+    ctx->prof_used = 0;
+    return PB_OK;
+}
+
 }  // namespace pb
 
 using namespace pb;
@@ -72,6 +86,8 @@ void free_all(pb_ctx *ctx) {
                     ctx->d, ctx->rres, ctx->st};
     for (void *p : bufs) ctx_free(ctx, p);
     cudaStreamSynchronize(ctx->stream);
+    for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
+    ctx->prof_ev.clear();
     if (ctx->host_scalar) cudaFreeHost(ctx->host_scalar);
     if (ctx->st_host) cudaFreeHost(ctx->st_host);
 }
@@ -140,6 +156,15 @@ pb_status launch_sub(pb_ctx *ctx, const double *a, const double *b, double *out)
     PB_LAUNCHED();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PB_OK : cuda_error(ctx, e, "sub kernel");
+}
+
+pb_status read_counter(pb_ctx *ctx, unsigned long long *host) {
+    cudaError_t e = cudaMemcpyAsync(ctx->host_scalar + 8, ctx->mv_count, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "counter readback");
+    memcpy(host, ctx->host_scalar + 8, sizeof(unsigned long long));
+    return PB_OK;
 }
 
 pb_status read_scalar(pb_ctx *ctx, const double *dev, double *host) {
@@ -225,8 +250,10 @@ pb_status pb_create(const double *centroids, const double *normals, const double
         if (e != cudaSuccess) s = cuda_error(ctx, e, "pinned scalars");
     }
     if (s == PB_OK) {
+        ctx->mv_count = (unsigned long long *)(ctx->scalar + 8);
         e = cudaMemsetAsync(ctx->tile_counters, 0, ctx->counters_len * sizeof(unsigned int), ctx->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->red_counter, 0, 16 * sizeof(unsigned int), ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->scalar, 0, 16 * sizeof(double), ctx->stream);
         if (e != cudaSuccess) s = cuda_error(ctx, e, "counter reset");
     }
     if (s == PB_OK) s = stage(ctx, centroids, 3 * N, &c_dev, "centroid staging");
@@ -291,6 +318,8 @@ pb_status pb_solve(pb_ctx *ctx, const pb_solve_opts *opts, const double *x0, dou
     }
     if (e != cudaSuccess) return cuda_error(ctx, e, "pb_solve: start vector");
 
+    unsigned long long mv_before = 0, mv_after = 0;
+    if ((s = read_counter(ctx, &mv_before)) != PB_OK) return s;
     int iters = 0, cycles = 0;
     double rel = 0.0;
     pb_status gs = gmres_solve(ctx, &o, ctx->b, ctx->x, x0 == nullptr, &iters, &cycles, &rel);
@@ -337,7 +366,10 @@ pb_status pb_solve(pb_ctx *ctx, const pb_solve_opts *opts, const double *x0, dou
         if (e != cudaSuccess) return cuda_error(ctx, e, "pb_solve: copy out");
     }
     ctx->x_valid = true;
+    if ((s = read_counter(ctx, &mv_after)) != PB_OK) return s;
+    if (ctx->prof_on && (s = profile_flush(ctx)) != PB_OK) return s;
     if (info) {
+        info->matvecs = (int64_t)(mv_after - mv_before);
         info->iters = total_it;
         info->cycles = total_cy;
         info->rel_resid = rel;
@@ -375,6 +407,43 @@ pb_status pb_get_info(pb_ctx *ctx, pb_ctx_info *info) {
     info->gauss_min = ctx->gauss_min;
     info->gauss_max = ctx->gauss_max;
     info->device_bytes = ctx->device_bytes;
+    return PB_OK;
+}
+
+pb_status pb_profile_enable(pb_ctx *ctx, int enable) {
+    if (!ctx) return set_error(nullptr, PB_ERR_ARG, "pb_profile_enable: NULL context");
+    if (enable && ctx->prof_ev.empty()) {
+        ctx->prof_ev.resize(2 * 1024, nullptr);
+        for (auto &ev : ctx->prof_ev) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) {
+                ctx->prof_ev.clear();
+                return cuda_error(ctx, e, "pb_profile_enable");
+            }
+        }
+    }
+    if (!enable) {
+        pb_status s = profile_flush(ctx);
+        if (s != PB_OK) return s;
+    }
+    ctx->prof_on = enable != 0;
+    return PB_OK;
+}
+
+pb_status pb_profile_read(pb_ctx *ctx, double *matvec_ms, int64_t *timed_launches, int64_t *evaluated, int reset) {
+    if (!ctx) return set_error(nullptr, PB_ERR_ARG, "pb_profile_read: NULL context");
+    pb_status s = profile_flush(ctx);
+    if (s != PB_OK) return s;
+    unsigned long long n = 0;
+    if ((s = read_counter(ctx, &n)) != PB_OK) return s;
+    if (matvec_ms) *matvec_ms = ctx->prof_ms;
+    if (timed_launches) *timed_launches = ctx->prof_launches;
+    if (evaluated) *evaluated = (int64_t)(n - ctx->prof_count_base);
+    if (reset) {
+        ctx->prof_ms = 0.0;
+        ctx->prof_launches = 0;
+        ctx->prof_count_base = n;
+    }
     return PB_OK;
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "pb.h"
 
 namespace pb {
@@ -129,6 +131,17 @@ struct pb_ctx {
     pb::GmresState *st = nullptr;
     pb::GmresState *st_host = nullptr;   // pinned
 
+    // device count of evaluated matrix-vector products (scalar[8] as uint64)
+    unsigned long long *mv_count = nullptr;
+
+    // optional event timing of the matvec launches (pb_profile_enable)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_used = 0;
+    double prof_ms = 0.0;
+    int64_t prof_launches = 0;
+    unsigned long long prof_count_base = 0;
+
     int64_t device_bytes = 0;
     char last_error[512] = {0};
 };
@@ -153,6 +166,9 @@ pb_status gauss_check(pb_ctx *ctx, double *gmin, double *gmax);
 // matvec.cu
 pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision prec, const int *skip_flag);
 int matvec_occupancy(pb_precision prec);
+
+// pb_api.cu: fold recorded matvec event pairs into ctx->prof_ms (syncs the stream)
+pb_status profile_flush(pb_ctx *ctx);
 
 // source_energy.cu
 pb_status source_launch(pb_ctx *ctx, double *b, pb_precision prec);
