@@ -156,6 +156,30 @@ pb_status pb_profile_enable(pb_ctx *ctx, int enable);
 pb_status pb_profile_read(pb_ctx *ctx, double *matvec_ms, int64_t *timed_launches, int64_t *evaluated,
                           int reset);
 
+/* No-allocation matrix-vector product.  The paper has no counterpart: this is
+ * a library convenience for callers that cannot call cudaMalloc (for example
+ * code running under a framework whose caching allocator already owns all of
+ * the device memory, or a latency-critical path where an allocation, which may
+ * synchronise the device, is not acceptable).  It computes the same y = A u as
+ * pb_matvec(..., PB_FP32PAIR) without a pb_ctx and without allocating:
+ *  - centroids, normals: device, N x 3 row-major FP64; areas: device, N FP64;
+ *    normals must already be unit length and areas > 0 (no validation pass);
+ *  - center: host, 3 doubles subtracted from every centroid before the FP32
+ *    cast (pass the bounding-box centre, as pb_create does; NULL = origin);
+ *  - u, y: device, 2N FP64 each, must not overlap; the caller owns them;
+ *  - the work is enqueued on cuda_stream (NULL = legacy default stream).
+ * Scratch lives in one 16 MiB file-scope static device array that every GPU
+ * loading the library keeps until the process exits.  Its arrival counters are
+ * cleared by every call; every call shares the array, so calls that overlap
+ * on the GPU race and must not be issued.  The first call on a device resolves
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  N above 2^24 = 16,777,216
+ * is rejected with PB_ERR_ARG (a fixed limit of the static scratch).  Errors:
+ * PB_ERR_ARG, PB_ERR_CUDA; messages via pb_last_error(NULL). */
+pb_status pb_matvec_f32_static(const double *centroids, const double *normals, const double *areas, int64_t N,
+                               const double *center, double eps1, double eps2, double kappa, const double *u,
+                               double *y, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

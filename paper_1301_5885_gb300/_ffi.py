@@ -60,6 +60,7 @@ SIGNATURES = {
     "pb_kernel_launches": (ctypes.c_uint64, []),
     "pb_profile_enable": (_I, [_VP, _I]),
     "pb_profile_read": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), ctypes.POINTER(_I64), _I]),
+    "pb_matvec_f32_static": (_I, [_VP, _VP, _VP, _I64, ctypes.POINTER(_D), _D, _D, _D, _VP, _VP, _VP]),
 }
 
 _LIB = None
@@ -255,6 +256,24 @@ def pb_profile_read(ctx: Context, reset: bool = False) -> dict:
     _check(lib().pb_profile_read(ctx.handle, ctypes.byref(ms), ctypes.byref(timed), ctypes.byref(ev),
                                  1 if reset else 0), ctx)
     return {"matvec_ms": ms.value, "timed_launches": timed.value, "evaluated": ev.value}
+
+
+def pb_matvec_f32_static(centroids, normals, areas, u, y, eps1: float, eps2: float, kappa: float,
+                         center=None, stream=None) -> None:
+    """y = A u in FP32 pairs without any device allocation (see include/pb.h).
+    centroids, normals, areas, u, y: contiguous float64 CUDA tensors."""
+    import torch
+    n = int(areas.numel())
+    for name, t, ln in (("centroids", centroids, 3 * n), ("normals", normals, 3 * n), ("areas", areas, n)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                and t.numel() == ln):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor with {ln} elements")
+    c = (ctypes.c_double * 3)(*[float(v) for v in center]) if center is not None else None
+    st = lib().pb_matvec_f32_static(centroids.data_ptr(), normals.data_ptr(), areas.data_ptr(), n,
+                                    ctypes.cast(c, ctypes.POINTER(ctypes.c_double)) if c is not None else None,
+                                    float(eps1), float(eps2), float(kappa), _device_vec(u, 2 * n, "u"),
+                                    _device_vec(y, 2 * n, "y"), _stream_ptr(stream))
+    _check(st)
 
 
 def pb_destroy(ctx: Context) -> None:
