@@ -47,7 +47,7 @@ PEAK_GPAIRS = SMS * 128 * SM_MAX_MHZ * 1e6 / FP32_OPS_PER_PAIR / 1e9
 # dram__bytes_read.sum + dram__bytes_write.sum of one matvec_f32_kernel launch
 # on the 81,920-triangle sphere, from the ncu capture summarised in
 # profiles/matvec_f32_kernel_sphere2_full.md; None once the kernel has changed.
-MATVEC_TRAFFIC_BYTES = {("matvec_f32_kernel", "sphere2"): 3988992}
+MATVEC_TRAFFIC_BYTES = {("matvec_f32_kernel", "sphere2"): 3988992}   # scalar kernel (variant 1)
 
 WORKLOADS = {
     "sphere2": "Kirkwood sphere R=20 A, icosphere level 6 (81,920 triangles), 20 charges in 0.8R, "
@@ -237,9 +237,12 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    variant_seen = []
+
     def step(c, nr, a, q, profile=False):
         ctx = pb.pb_create(c, nr, a, q, prob.eps1, prob.eps2, prob.kappa, stream=stream)
         try:
+            variant_seen.append(pb.pb_matvec_get_config(ctx)["variant"])
             if profile:
                 pb.pb_profile_enable(ctx, True)
             info = pb.pb_solve(ctx, restart=args.restart, tol=args.tol, maxit=2000, prec=args.prec)
@@ -292,9 +295,12 @@ def run_ours(args):
     avg_ms = mv_ms / max(1, mv_n)
     achieved = pairs_per_mv / (avg_ms * 1e-3) / 1e9
     mv_share = mv_ms / total_ms
+    variant = variant_seen[-1]
 
     result = None
-    kname = "matvec_f32_kernel" if args.prec == "fp32pair" else "matvec_f64_kernel"
+    kname = "matvec_f64_kernel"
+    if args.prec == "fp32pair":
+        kname = {1: "matvec_f32_kernel", 2: "matvec_f32x2_kernel<2>", 3: "matvec_f32x2_kernel<4>"}[variant]
     if rank == 0:
         ref_e = golden_energy(args.workload)
         energies = [i.energy_kcal for i in infos]

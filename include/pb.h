@@ -156,6 +156,18 @@ pb_status pb_profile_enable(pb_ctx *ctx, int enable);
 pb_status pb_profile_read(pb_ctx *ctx, double *matvec_ms, int64_t *timed_launches, int64_t *evaluated,
                           int reset);
 
+/* Kernel choice for the FP32-pair product (a tuning knob of this library; the
+ * paper has a single FP64 kernel).  variant: 1 = scalar FP32, 4 targets per
+ * thread; 2 = packed f32x2, 2 targets per thread; 3 = packed f32x2, 4 targets
+ * per thread; 0 = the stored or built-in default.  ctas_per_sm: resident CTAs
+ * per SM of the persistent grid, 0 = as many as fit.  Results differ between
+ * variants only by FP32 rounding.  pb_matvec_autotune times every candidate
+ * (reps launches each) on the context's geometry, keeps the fastest, and
+ * stores the choice for later contexts of similar N on the same device. */
+pb_status pb_matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm);
+pb_status pb_matvec_get_config(pb_ctx *ctx, int *variant, int *ctas_per_sm, int64_t *ctas);
+pb_status pb_matvec_autotune(pb_ctx *ctx, int reps, int *variant, int *ctas_per_sm, double *best_ms);
+
 /* No-allocation matrix-vector product.  The paper has no counterpart: this is
  * a library convenience for callers that cannot call cudaMalloc (for example
  * code running under a framework whose caching allocator already owns all of

@@ -61,6 +61,9 @@ SIGNATURES = {
     "pb_profile_enable": (_I, [_VP, _I]),
     "pb_profile_read": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), ctypes.POINTER(_I64), _I]),
     "pb_matvec_f32_static": (_I, [_VP, _VP, _VP, _I64, ctypes.POINTER(_D), _D, _D, _D, _VP, _VP, _VP]),
+    "pb_matvec_configure": (_I, [_VP, _I, _I]),
+    "pb_matvec_get_config": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64)]),
+    "pb_matvec_autotune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
 }
 
 _LIB = None
@@ -274,6 +277,22 @@ def pb_matvec_f32_static(centroids, normals, areas, u, y, eps1: float, eps2: flo
                                     float(eps1), float(eps2), float(kappa), _device_vec(u, 2 * n, "u"),
                                     _device_vec(y, 2 * n, "y"), _stream_ptr(stream))
     _check(st)
+
+
+def pb_matvec_configure(ctx: Context, variant: int = 0, ctas_per_sm: int = 0) -> None:
+    _check(lib().pb_matvec_configure(ctx.handle, int(variant), int(ctas_per_sm)), ctx)
+
+
+def pb_matvec_get_config(ctx: Context) -> dict:
+    v, c, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    _check(lib().pb_matvec_get_config(ctx.handle, ctypes.byref(v), ctypes.byref(c), ctypes.byref(g)), ctx)
+    return {"variant": v.value, "ctas_per_sm": c.value, "ctas": g.value}
+
+
+def pb_matvec_autotune(ctx: Context, reps: int = 3) -> dict:
+    v, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().pb_matvec_autotune(ctx.handle, int(reps), ctypes.byref(v), ctypes.byref(c), ctypes.byref(ms)), ctx)
+    return {"variant": v.value, "ctas_per_sm": c.value, "ms": ms.value}
 
 
 def pb_destroy(ctx: Context) -> None:

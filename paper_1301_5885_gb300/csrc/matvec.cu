@@ -24,6 +24,7 @@
 // diagonal term.
 #include <math.h>
 
+#include "fastmath.cuh"
 #include "pb_internal.cuh"
 
 namespace pb {
@@ -44,18 +45,6 @@ StreamKPlan make_plan(int64_t n, int target_tile, int source_tile, int64_t ctas_
 }
 
 namespace {
-
-__device__ __forceinline__ float rsqrt_approx(float x) {
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ float exp2_approx(float x) {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 struct F32Params {
     float eps, inv_eps, kappa, neg_kappa_log2e;
@@ -212,6 +201,136 @@ matvec_f32_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
 }
 
 // ---------------------------------------------------------------------------
+// The same FP32-pair product with packed f32x2 arithmetic: one instruction
+// evaluates a step of two pairs (one target against two sources), which
+// halves the issue slots of the FP32 work so that the FP32 pipe, not the
+// instruction issue, bounds the kernel.  Sources are staged in shared memory
+// as pairs (2q, 2q+1), four float4 per pair:
+//   {-x0, -x1, -y0, -y1}  {-z0, -z1, nx0, nx1}  {ny0, ny1, nz0, nz1}  {Wdphi0, Wdphi1, Wphi0, Wphi1}
+// (W carries the 1/(4 pi)).  Each thread owns T targets, duplicated into both
+// halves of register pairs.  The singular self pair (and any pair at zero
+// distance) is removed by clamping 1/rho at 1e12: then rho = r2 * (1/rho) is
+// exactly 0, exp2(0) is exactly 1, c_x = c_y = 0, and every term of K1..K4 is an
+// exact zero, with no infinity formed.  Real pairs have 1/rho < 1e12 (rho > 1e-12 A).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_dup(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+constexpr float kInvRhoMax = 1e12f;
+
+template <int T>
+__global__ void __launch_bounds__(kF32Threads)
+matvec_f32x2_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm,
+                    const double *__restrict__ u, int64_t N, F32Params prm, StreamKPlan plan,
+                    double *__restrict__ partials, unsigned int *__restrict__ counters,
+                    double *__restrict__ y, const int *__restrict__ skip, unsigned long long *__restrict__ evaluated) {
+    constexpr int BS = kF32Threads, TT = BS * T, TS = kF32SourceTile, TQ = TS / 2;
+    static_assert(TQ == BS, "one source pair per thread when staging");
+    if (skip != nullptr && *((volatile const int *)skip)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
+    __shared__ float4 s_a[TQ], s_b[TQ], s_c[TQ], s_d[TQ];
+
+    const int tid = threadIdx.x;
+    const int64_t c = blockIdx.x;
+    const int64_t S = plan.source_tiles;
+    int64_t p = sk_begin(c, plan.work, plan.ctas);
+    const int64_t pend = sk_begin(c + 1, plan.work, plan.ctas);
+    const float2 eps2 = p_dup(prm.eps), ieps2 = p_dup(prm.inv_eps), kap2 = p_dup(prm.kappa);
+    const float2 nk2 = p_dup(prm.neg_kappa_log2e);
+    const float2 one2 = p_dup(1.f), mone2 = p_dup(-1.f), three2 = p_dup(3.f), mthree2 = p_dup(-3.f);
+
+    while (p < pend) {
+        const int64_t a = p / S;
+        const int64_t s_first = p % S;
+        const int64_t s_end = (S < s_first + (pend - p)) ? S : s_first + (pend - p);
+
+        float2 xi[T], yi[T], zi[T], nxi[T], nyi[T], nzi[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            int64_t i = a * TT + t * BS + tid;
+            if (i > N - 1) i = N - 1;
+            const float4 q = pos[i], n = nrm[i];
+            xi[t] = p_dup(q.x); yi[t] = p_dup(q.y); zi[t] = p_dup(q.z);
+            nxi[t] = p_dup(n.x); nyi[t] = p_dup(n.y); nzi[t] = p_dup(n.z);
+        }
+        double acc1[T], acc2[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) { acc1[t] = 0.0; acc2[t] = 0.0; }
+
+        for (int64_t s = s_first; s < s_end; ++s) {
+            __syncthreads();
+            {
+                // stage source pair (2 tid, 2 tid + 1); a missing second source
+                // repeats the first with zero weights
+                const int64_t j0 = s * TS + 2 * tid;
+                if (j0 < N) {
+                    const int64_t j1 = (j0 + 1 < N) ? j0 + 1 : j0;
+                    const float4 p0 = pos[j0], p1 = pos[j1], n0 = nrm[j0], n1 = nrm[j1];
+                    const float w0 = p0.w, w1 = (j0 + 1 < N) ? p1.w : 0.f;
+                    s_a[tid] = make_float4(-p0.x, -p1.x, -p0.y, -p1.y);
+                    s_b[tid] = make_float4(-p0.z, -p1.z, n0.x, n1.x);
+                    s_c[tid] = make_float4(n0.y, n1.y, n0.z, n1.z);
+                    s_d[tid] = make_float4((float)u[N + j0] * w0, (float)u[N + j1] * w1, (float)u[j0] * w0,
+                                           (float)u[j1] * w1);
+                }
+            }
+            __syncthreads();
+            const int64_t rem = N - s * TS;
+            const int npairs = (int)(((rem < TS) ? rem : TS) + 1) / 2;
+            float2 f1[T], f2[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) { f1[t] = p_dup(0.f); f2[t] = p_dup(0.f); }
+#pragma unroll 2
+            for (int q = 0; q < npairs; ++q) {
+                const float4 A = s_a[q], B = s_b[q], C = s_c[q], D = s_d[q];
+                const float2 mx = make_float2(A.x, A.y), my = make_float2(A.z, A.w), mz = make_float2(B.x, B.y);
+                const float2 snx = make_float2(B.z, B.w), sny = make_float2(C.x, C.y), snz = make_float2(C.z, C.w);
+                const float2 wpsi = make_float2(D.x, D.y), wphi = make_float2(D.z, D.w);
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const float2 dx = p_add(xi[t], mx), dy = p_add(yi[t], my), dz = p_add(zi[t], mz);
+                    const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
+                    float2 inv;
+                    inv.x = fminf(rsqrt_approx(r2.x), kInvRhoMax);
+                    inv.y = fminf(rsqrt_approx(r2.y), kInvRhoMax);
+                    const float2 rho = p_mul(r2, inv);
+                    const float2 arg = p_mul(nk2, rho);
+                    float2 e;
+                    e.x = exp2_approx(arg.x);
+                    e.y = exp2_approx(arg.y);
+                    const float2 kr = p_mul(kap2, rho);
+                    const float2 e1 = p_fma(e, kr, e);                    // e (1 + kappa rho)
+                    const float2 inv2 = p_mul(inv, inv);
+                    const float2 inv3 = p_mul(inv2, inv);
+                    const float2 cx = p_fma(dx, nxi[t], p_fma(dy, nyi[t], p_mul(dz, nzi[t])));
+                    const float2 cy = p_fma(dx, snx, p_fma(dy, sny, p_mul(dz, snz)));
+                    const float2 nn = p_fma(nxi[t], snx, p_fma(nyi[t], sny, p_mul(nzi[t], snz)));
+                    const float2 k1 = p_mul(p_fma(e, mone2, one2), inv);   // (1 - e)/rho
+                    const float2 k2 = p_mul(p_mul(p_fma(eps2, e1, mone2), cy), inv3);
+                    const float2 k3 = p_mul(p_mul(p_fma(e1, ieps2, mone2), cx), inv3);
+                    const float2 p3 = p_fma(kr, p_add(kr, three2), three2);   // 3 + 3 kr + kr^2
+                    const float2 e3 = p_fma(e, p3, mthree2);
+                    const float2 ccy = p_mul(p_mul(e3, cx), cy);
+                    const float2 k4 = p_mul(p_fma(p_neg(ccy), inv2, p_fma(e1, nn, p_neg(nn))), inv3);
+                    f1[t] = p_fma(k1, wpsi, p_fma(k2, wphi, f1[t]));
+                    f2[t] = p_fma(k3, wpsi, p_fma(k4, wphi, f2[t]));
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                acc1[t] += (double)f1[t].x + (double)f1[t].y;
+                acc2[t] += (double)f2[t].x + (double)f2[t].y;
+            }
+        }
+        finish_segment<TT, T, BS>(plan, a, c, acc1, acc2, u, N, prm.diag1, prm.diag2, partials, counters, y);
+        p += s_end - s_first;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Plain FP64 path: every pair and every sum in FP64.
 // ---------------------------------------------------------------------------
 struct F64Params {
@@ -311,9 +430,23 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         prm.diag1 = diag1;
         prm.diag2 = diag2;
         const StreamKPlan &pl = ctx->plan32;
-        matvec_f32_kernel<<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(
-            ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,
-            ctx->mv_count);
+        switch (ctx->f32_variant) {
+            case MV_F32_SCALAR_T4:
+                matvec_f32_kernel<<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(
+                    ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,
+                    ctx->mv_count);
+                break;
+            case MV_F32_PACKED_T4:
+                matvec_f32x2_kernel<4><<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(
+                    ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,
+                    ctx->mv_count);
+                break;
+            default:
+                matvec_f32x2_kernel<2><<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(
+                    ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,
+                    ctx->mv_count);
+                break;
+        }
     } else {
         F64Params prm{ctx->eps, 1.0 / ctx->eps, ctx->kappa, diag1, diag2};
         const StreamKPlan &pl = ctx->plan64;
@@ -335,10 +468,49 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
 int matvec_occupancy(pb_precision prec) {
     int n = 0;
     if (prec == PB_FP32PAIR)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32_kernel, kF32Threads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f64_kernel, kF64Threads, 0);
+        return matvec_f32_occupancy(MV_F32_PACKED_T2);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f64_kernel, kF64Threads, 0);
     return n < 1 ? 1 : n;
+}
+
+int matvec_f32_occupancy(int variant) {
+    int n = 0;
+    switch (variant) {
+        case MV_F32_SCALAR_T4:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32_kernel, kF32Threads, 0);
+            break;
+        case MV_F32_PACKED_T4:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<4>, kF32Threads, 0);
+            break;
+        default:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<2>, kF32Threads, 0);
+            break;
+    }
+    return n < 1 ? 1 : n;
+}
+
+StreamKPlan matvec_f32_plan(pb_ctx *ctx, int variant, int ctas_per_sm) {
+    int occ = matvec_f32_occupancy(variant);
+    if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
+    return make_plan(ctx->N, kF32Threads * f32_variant_targets(variant), kF32SourceTile, (int64_t)ctx->num_sms * occ);
+}
+
+int64_t plan_partials(const StreamKPlan &pl, int target_tile) {
+    return pl.target_tiles * pl.max_segments * 2 * target_tile;
+}
+
+pb_status matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm) {
+    if (variant < 1 || variant > kNumF32Variants)
+        return set_error(ctx, PB_ERR_ARG, "matvec variant %d is not one of 1..%d", variant, kNumF32Variants);
+    if (ctas_per_sm < 0) return set_error(ctx, PB_ERR_ARG, "ctas_per_sm must be >= 0");
+    StreamKPlan pl = matvec_f32_plan(ctx, variant, ctas_per_sm);
+    if (plan_partials(pl, kF32Threads * f32_variant_targets(variant)) > ctx->partials_len ||
+        pl.target_tiles > ctx->counters_len)
+        return set_error(ctx, PB_ERR_ARG, "matvec configuration exceeds the context's scratch");
+    ctx->f32_variant = variant;
+    ctx->f32_ctas_per_sm = ctas_per_sm;
+    ctx->plan32 = pl;
+    return PB_OK;
 }
 
 }  // namespace pb

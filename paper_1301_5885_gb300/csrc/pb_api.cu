@@ -226,13 +226,22 @@ pb_status pb_create(const double *centroids, const double *normals, const double
     double *c_dev = nullptr, *n_dev = nullptr, *a_dev = nullptr;
     const int64_t N2 = 2 * N;
     if (s == PB_OK) {
-        ctx->plan32 = make_plan(N, kF32TargetTile, kF32SourceTile, (int64_t)ctx->num_sms * matvec_occupancy(PB_FP32PAIR));
+        // scratch sized for every kernel variant at any CTA count per SM up to
+        // its occupancy (fewer CTAs never need more segments)
         ctx->plan64 = make_plan(N, kF64TargetTile, kF64SourceTile, (int64_t)ctx->num_sms * matvec_occupancy(PB_FP64));
-        int64_t p32 = ctx->plan32.target_tiles * ctx->plan32.max_segments * 2 * kF32TargetTile;
-        int64_t p64 = ctx->plan64.target_tiles * ctx->plan64.max_segments * 2 * kF64TargetTile;
-        ctx->partials_len = p32 > p64 ? p32 : p64;
-        ctx->counters_len = ctx->plan32.target_tiles > ctx->plan64.target_tiles ? ctx->plan32.target_tiles
-                                                                                  : ctx->plan64.target_tiles;
+        ctx->partials_len = plan_partials(ctx->plan64, kF64TargetTile);
+        ctx->counters_len = ctx->plan64.target_tiles;
+        for (int v = 1; v <= kNumF32Variants; ++v) {
+            StreamKPlan pl = matvec_f32_plan(ctx, v, 0);
+            int64_t need = plan_partials(pl, kF32Threads * f32_variant_targets(v));
+            if (need > ctx->partials_len) ctx->partials_len = need;
+            if (pl.target_tiles > ctx->counters_len) ctx->counters_len = pl.target_tiles;
+        }
+        int v = 0, cps = 0;
+        default_f32_config(ctx, &v, &cps);
+        ctx->f32_variant = v;
+        ctx->f32_ctas_per_sm = cps;
+        ctx->plan32 = matvec_f32_plan(ctx, v, cps);
         ctx->red_len = (int64_t)(kMaxRestart + 1) * 2 * ctx->num_sms;
     }
     if (s == PB_OK) s = ctx_alloc(ctx, (void **)&ctx->g64, 7 * N * sizeof(double), "FP64 geometry");

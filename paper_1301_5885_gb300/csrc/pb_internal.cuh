@@ -30,6 +30,11 @@ constexpr int kF32Threads = 128;
 constexpr int kF32TargetsPerThread = 4;
 constexpr int kF32TargetTile = kF32Threads * kF32TargetsPerThread;
 constexpr int kF32SourceTile = 256;
+// FP32-pair kernel variants (one is chosen per context, by default or by the
+// autotuner): targets per thread and scalar or packed f32x2 arithmetic.
+enum MatvecVariant { MV_F32_SCALAR_T4 = 1, MV_F32_PACKED_T2 = 2, MV_F32_PACKED_T4 = 3 };
+constexpr int kNumF32Variants = 3;
+__host__ __device__ constexpr int f32_variant_targets(int v) { return v == MV_F32_PACKED_T2 ? 2 : 4; }
 // FP64 kernel: 128 threads x 1 target, 128 sources per source tile.
 constexpr int kF64Threads = 128;
 constexpr int kF64TargetTile = kF64Threads;
@@ -109,6 +114,8 @@ struct pb_ctx {
     // matvec scratch: per (target tile, segment) partial row sums, and one
     // arrival counter per target tile (left at zero between launches)
     pb::StreamKPlan plan32{}, plan64{};
+    int f32_variant = 0;         // MatvecVariant of the FP32-pair product
+    int f32_ctas_per_sm = 0;
     double *partials = nullptr;
     int64_t partials_len = 0;
     unsigned int *tile_counters = nullptr;
@@ -166,6 +173,14 @@ pb_status gauss_check(pb_ctx *ctx, double *gmin, double *gmax);
 // matvec.cu
 pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision prec, const int *skip_flag);
 int matvec_occupancy(pb_precision prec);
+int matvec_f32_occupancy(int variant);
+// plan of an FP32 variant at a CTA count per SM (0 = the variant's occupancy)
+StreamKPlan matvec_f32_plan(pb_ctx *ctx, int variant, int ctas_per_sm);
+// partial-row capacity (doubles) a plan needs
+int64_t plan_partials(const StreamKPlan &pl, int target_tile);
+pb_status matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm);
+// tune.cu: the stored or built-in FP32 kernel choice for this context's size
+void default_f32_config(pb_ctx *ctx, int *variant, int *ctas_per_sm);
 
 // pb_api.cu: fold recorded matvec event pairs into ctx->prof_ms (syncs the stream)
 pb_status profile_flush(pb_ctx *ctx);

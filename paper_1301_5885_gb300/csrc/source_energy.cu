@@ -10,6 +10,7 @@
 // distance are dropped.
 #include <math.h>
 
+#include "fastmath.cuh"
 #include "pb_internal.cuh"
 #include "reduce.cuh"
 
@@ -18,17 +19,6 @@ namespace {
 
 constexpr int kSrcThreads = 256;
 constexpr int kChargeTile = 256;
-
-__device__ __forceinline__ float rsqrt_approx(float x) {
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ float exp2_approx(float x) {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 template <bool F32>
 __global__ void __launch_bounds__(kSrcThreads)

@@ -1,0 +1,152 @@
+// tune.cu -- choice of the FP32-pair matvec kernel variant and grid size.
+//
+// The variants (scalar or packed f32x2 arithmetic, 2 or 4 targets per thread)
+// and the number of resident CTAs per SM trade registers, occupancy and
+// instruction issue differently at different N.  pb_matvec_autotune times each
+// candidate on the context's own geometry and keeps the fastest; the choice is
+// also stored in a process-wide table keyed by (device, N bucket) so that later
+// contexts of similar size start from it.  Without a stored choice a context
+// uses the built-in default.
+#include <math.h>
+#include <mutex>
+
+#include "pb_internal.cuh"
+
+namespace pb {
+namespace {
+
+// Built-in default, from timings on GB300: packed f32x2 with 4 targets per
+// thread is fastest once there are enough target tiles to fill the GPU
+// (798 vs 795 Gpairs/s at N = 81,920; the scalar kernel gives 627); below
+// that the 2-target variant keeps more CTAs busy (512 vs 400 Gpairs/s at
+// N = 5,120).
+constexpr int64_t kPackedT4MinN = 32768;
+constexpr int kBuckets = 256;
+
+struct TuneEntry {
+    bool set = false;
+    int variant = 0;
+    int ctas_per_sm = 0;
+};
+std::mutex g_tune_mu;
+TuneEntry g_tune[8][kBuckets];   // [device % 8][bucket]
+
+// quarter-octave bucket of N
+int bucket_of(int64_t n) {
+    int b = (int)floor(4.0 * log2((double)(n < 1 ? 1 : n)));
+    return b < 0 ? 0 : (b >= kBuckets ? kBuckets - 1 : b);
+}
+
+}  // namespace
+
+void default_f32_config(pb_ctx *ctx, int *variant, int *ctas_per_sm) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const TuneEntry &e = g_tune[ctx->device & 7][bucket_of(ctx->N)];
+    if (e.set) {
+        *variant = e.variant;
+        *ctas_per_sm = e.ctas_per_sm;
+    } else {
+        *variant = ctx->N >= kPackedT4MinN ? MV_F32_PACKED_T4 : MV_F32_PACKED_T2;
+        *ctas_per_sm = 0;
+    }
+}
+
+}  // namespace pb
+
+using namespace pb;
+
+extern "C" {
+
+pb_status pb_matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm) {
+    if (!ctx) return set_error(nullptr, PB_ERR_ARG, "pb_matvec_configure: NULL context");
+    if (variant == 0) {
+        int v = 0, c = 0;
+        default_f32_config(ctx, &v, &c);
+        return matvec_configure(ctx, v, ctas_per_sm > 0 ? ctas_per_sm : c);
+    }
+    return matvec_configure(ctx, variant, ctas_per_sm);
+}
+
+pb_status pb_matvec_get_config(pb_ctx *ctx, int *variant, int *ctas_per_sm, int64_t *ctas) {
+    if (!ctx) return set_error(nullptr, PB_ERR_ARG, "pb_matvec_get_config: NULL context");
+    if (variant) *variant = ctx->f32_variant;
+    if (ctas_per_sm) *ctas_per_sm = ctx->f32_ctas_per_sm;
+    if (ctas) *ctas = ctx->plan32.ctas;
+    return PB_OK;
+}
+
+pb_status pb_matvec_autotune(pb_ctx *ctx, int reps, int *variant, int *ctas_per_sm, double *best_ms) {
+    if (!ctx) return set_error(nullptr, PB_ERR_ARG, "pb_matvec_autotune: NULL context");
+    if (reps < 1) reps = 3;
+    const int64_t n2 = 2 * ctx->N;
+    double *u = nullptr, *y = nullptr;
+    pb_status s = ctx_alloc(ctx, (void **)&u, n2 * sizeof(double), "autotune u");
+    if (s == PB_OK) s = ctx_alloc(ctx, (void **)&y, n2 * sizeof(double), "autotune y");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaSuccess;
+    if (s == PB_OK) {
+        ce = cudaMemsetAsync(u, 0, n2 * sizeof(double), ctx->stream);
+        if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+        if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+        if (ce != cudaSuccess) s = cuda_error(ctx, ce, "pb_matvec_autotune");
+    }
+    const int keep_v = ctx->f32_variant, keep_c = ctx->f32_ctas_per_sm;
+    int best_v = keep_v, best_c = keep_c;
+    double best = INFINITY;
+    const bool prof = ctx->prof_on;
+    ctx->prof_on = false;
+    for (int v = 1; v <= kNumF32Variants && s == PB_OK; ++v) {
+        const int occ = matvec_f32_occupancy(v);
+        int tried[4], ntried = 0;
+        const int cands[4] = {occ, occ - 1, 4, 2};
+        for (int ci = 0; ci < 4 && s == PB_OK; ++ci) {
+            const int c = cands[ci];
+            if (c < 1 || c > occ) continue;
+            bool dup = false;
+            for (int k = 0; k < ntried; ++k) dup |= (tried[k] == c);
+            if (dup) continue;
+            tried[ntried++] = c;
+            if ((s = matvec_configure(ctx, v, c)) != PB_OK) break;
+            if ((s = matvec_launch(ctx, u, y, PB_FP32PAIR, nullptr)) != PB_OK) break;   // warm-up
+            cudaEventRecord(e0, ctx->stream);
+            for (int r = 0; r < reps && s == PB_OK; ++r) s = matvec_launch(ctx, u, y, PB_FP32PAIR, nullptr);
+            cudaEventRecord(e1, ctx->stream);
+            if (s != PB_OK) break;
+            ce = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (ce != cudaSuccess) {
+                s = cuda_error(ctx, ce, "pb_matvec_autotune timing");
+                break;
+            }
+            if (ms / reps < best) {
+                best = ms / reps;
+                best_v = v;
+                best_c = c;
+            }
+        }
+    }
+    ctx->prof_on = prof;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ctx_free(ctx, u);
+    ctx_free(ctx, y);
+    if (s != PB_OK) {
+        matvec_configure(ctx, keep_v, keep_c);
+        return s;
+    }
+    if ((s = matvec_configure(ctx, best_v, best_c)) != PB_OK) return s;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        TuneEntry &e = g_tune[ctx->device & 7][bucket_of(ctx->N)];
+        e.set = true;
+        e.variant = best_v;
+        e.ctas_per_sm = best_c;
+    }
+    if (variant) *variant = best_v;
+    if (ctas_per_sm) *ctas_per_sm = best_c;
+    if (best_ms) *best_ms = best;
+    return PB_OK;
+}
+
+}  // extern "C"

@@ -77,22 +77,58 @@ def test_matvec_fp64_matches_oracle(name, surf, kappa):
     assert np.max(np.abs(y - ref)) <= 1e-9 * np.max(np.abs(ref))
 
 
+F32_VARIANTS = [1, 2, 3]   # scalar T4, packed f32x2 T2, packed f32x2 T4
+
+
 @pytest.mark.parametrize("name,surf", SURFACES, ids=[s[0] for s in SURFACES])
 @pytest.mark.parametrize("kappa", [0.1257, 0.0])
-def test_matvec_fp32pair_matches_oracle(name, surf, kappa):
+@pytest.mark.parametrize("variant", F32_VARIANTS)
+def test_matvec_fp32pair_matches_oracle(name, surf, kappa, variant):
     u = _u(surf.n, 2)
     with _ctx(surf, kappa=kappa) as ctx:
+        _pb().pb_matvec_configure(ctx, variant, 0)
         y = _gpu_matvec(ctx, u, "fp32pair")
     ref = oracle.matvec(surf, 80.0, kappa, u)
     assert np.all(np.isfinite(y))
     assert np.linalg.norm(y - ref) <= 2e-5 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32pair"])
-def test_matvec_is_identity_without_jump_or_salt(prec):
+@pytest.mark.parametrize("variant", F32_VARIANTS)
+@pytest.mark.parametrize("ctas_per_sm", [1, 2])
+def test_matvec_fp32pair_small_grids_match_oracle(variant, ctas_per_sm):
+    """Fewer resident CTAs per SM changes the stream-K split (more tiles per CTA)."""
+    surf = pi.icosphere(6.0, 4)
+    u = _u(surf.n, 12)
+    with _ctx(surf) as ctx:
+        _pb().pb_matvec_configure(ctx, variant, ctas_per_sm)
+        y = _gpu_matvec(ctx, u, "fp32pair")
+    ref = oracle.matvec(surf, 80.0, 0.1257, u)
+    assert np.linalg.norm(y - ref) <= 2e-5 * np.linalg.norm(ref)
+
+
+def test_autotune_picks_a_valid_variant_with_the_same_result():
+    pb = _pb()
+    surf = pi.icosphere(8.0, 5)
+    u = _u(surf.n, 13)
+    with _ctx(surf) as ctx:
+        y0 = _gpu_matvec(ctx, u, "fp32pair")
+        choice = pb.pb_matvec_autotune(ctx, reps=2)
+        assert choice["variant"] in F32_VARIANTS and choice["ms"] > 0
+        cfg = pb.pb_matvec_get_config(ctx)
+        assert cfg["variant"] == choice["variant"] and cfg["ctas"] >= 1
+        y1 = _gpu_matvec(ctx, u, "fp32pair")
+    assert np.linalg.norm(y1 - y0) <= 2e-5 * np.linalg.norm(y0)
+    with pytest.raises(pb.PBError):
+        with _ctx(surf) as ctx:
+            pb.pb_matvec_configure(ctx, 7, 0)
+
+
+@pytest.mark.parametrize("prec,variant", [("fp64", 0), ("fp32pair", 1), ("fp32pair", 2), ("fp32pair", 3)])
+def test_matvec_is_identity_without_jump_or_salt(prec, variant):
     surf = pi.icosphere(2.0, 3)
     u = _u(surf.n, 3)
     with _ctx(surf, eps1=2.0, eps2=2.0, kappa=0.0) as ctx:
+        _pb().pb_matvec_configure(ctx, variant, 0)
         y = _gpu_matvec(ctx, u, prec)
     assert np.array_equal(y, u)
 
@@ -107,13 +143,14 @@ def test_single_element_has_only_the_diagonal(prec):
     assert y[1] == 0.5 * (1 + 1 / 80.0) * -1.3
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32pair"])
-def test_duplicate_centroids_are_dropped_like_the_self_term(prec):
+@pytest.mark.parametrize("prec,variant", [("fp64", 0), ("fp32pair", 1), ("fp32pair", 2), ("fp32pair", 3)])
+def test_duplicate_centroids_are_dropped_like_the_self_term(prec, variant):
     base = pi.icosphere(2.0, 2)
     idx = np.concatenate([np.arange(base.n), [7, 7, 100]])
     surf = base.subset(idx)
     u = _u(surf.n, 4)
     with _ctx(surf) as ctx:
+        _pb().pb_matvec_configure(ctx, variant, 0)
         y = _gpu_matvec(ctx, u, prec)
     ref = oracle.matvec(surf, 80.0, 0.1257, u)
     tol = 1e-10 if prec == "fp64" else 2e-5
