@@ -46,8 +46,9 @@ SM_MAX_MHZ = 2070.0
 PEAK_GPAIRS = SMS * 128 * SM_MAX_MHZ * 1e6 / FP32_OPS_PER_PAIR / 1e9
 # dram__bytes_read.sum + dram__bytes_write.sum of one matvec_f32_kernel launch
 # on the 81,920-triangle sphere, from the ncu capture summarised in
-# profiles/matvec_f32_kernel_sphere2_full.md; None once the kernel has changed.
+# profiles/matvec_f32x2_kernel_sphere2_full.md; None once the kernel has changed.
 MATVEC_TRAFFIC_BYTES = {("matvec_f32_kernel", "sphere2"): 3988992}   # scalar kernel (variant 1)
+MATVEC_TRAFFIC_BYTES[("matvec_f32x2_kernel<4>", "sphere2")] = 3991296   # profiles/matvec_f32x2_kernel_sphere2_full.md
 
 WORKLOADS = {
     "sphere2": "Kirkwood sphere R=20 A, icosphere level 6 (81,920 triangles), 20 charges in 0.8R, "

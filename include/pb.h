@@ -156,6 +156,38 @@ pb_status pb_profile_enable(pb_ctx *ctx, int enable);
 pb_status pb_profile_read(pb_ctx *ctx, double *matvec_ms, int64_t *timed_launches, int64_t *evaluated,
                           int reset);
 
+/* Batched solves (many surfaces of uneven N, each with 1..8 charge sets).
+ * ctxs[s]: a context per surface (its geometry is used; its own charges are
+ * not); charges[s]: host array of nrhs[s] charge sets of nc[s] rows each
+ * (nrhs[s] x nc[s] x 4, rows x, y, z, Q).  Every (surface, charge set) pair is
+ * a GMRES instance (Section 2.4, restarted, x0 = 0) solved with FP32-pair
+ * products; all instances advance in lockstep and each lockstep product is one
+ * persistent launch over all surfaces that evaluates K1..K4 once per pair for
+ * all charge sets of a surface.  All work runs on ctxs[0]'s stream; the other
+ * contexts must not be in use meanwhile.  use_graph != 0 captures one restart
+ * cycle of the whole batch in a CUDA graph and replays it (ignored on the
+ * legacy default stream).  energies: host array of sum(nrhs) doubles (kcal/mol,
+ * Eq. (14)), in surface-major order.  Returns PB_ERR_NOCONV if an instance
+ * reached maxit (energies still filled).  This is a library extension for
+ * throughput; the paper solves one molecule per run. */
+typedef struct {
+    int instances;        /* sum of nrhs */
+    int converged;
+    int cycles;           /* lockstep restart cycles */
+    int iters_max;        /* largest Arnoldi step count of an instance */
+    int64_t iters_sum;
+    double rel_resid_max; /* largest final true relative residual */
+    int rhs_width;        /* charge sets per product kernel (1, 2, 4 or 8) */
+    int64_t ctas;         /* persistent CTAs of the product kernel */
+    int64_t pair_evals;   /* K1..K4 pair evaluations, sum over products of N(N-1) */
+    int64_t pair_products;/* pair evaluations times the charge sets they served */
+    int64_t matvec_launches;
+} pb_batch_info;
+
+pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double *const *charges, const int64_t *nc,
+                         const int *nrhs, const pb_solve_opts *opts, int use_graph, double *energies,
+                         pb_batch_info *info);
+
 /* Kernel choice for the FP32-pair product (a tuning knob of this library; the
  * paper has a single FP64 kernel).  variant: 1 = scalar FP32, 4 targets per
  * thread; 2 = packed f32x2, 2 targets per thread; 3 = packed f32x2, 4 targets

@@ -37,6 +37,13 @@ class _Info(ctypes.Structure):
                 ("refine_steps", ctypes.c_int), ("matvecs", ctypes.c_int64)]
 
 
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("instances", ctypes.c_int), ("converged", ctypes.c_int), ("cycles", ctypes.c_int),
+                ("iters_max", ctypes.c_int), ("iters_sum", ctypes.c_int64), ("rel_resid_max", ctypes.c_double),
+                ("rhs_width", ctypes.c_int), ("ctas", ctypes.c_int64), ("pair_evals", ctypes.c_int64),
+                ("pair_products", ctypes.c_int64), ("matvec_launches", ctypes.c_int64)]
+
+
 class _CtxInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nc", ctypes.c_int64), ("eps1", ctypes.c_double),
                 ("eps2", ctypes.c_double), ("kappa", ctypes.c_double), ("center", ctypes.c_double * 3),
@@ -62,6 +69,8 @@ SIGNATURES = {
     "pb_profile_read": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), ctypes.POINTER(_I64), _I]),
     "pb_matvec_f32_static": (_I, [_VP, _VP, _VP, _I64, ctypes.POINTER(_D), _D, _D, _D, _VP, _VP, _VP]),
     "pb_matvec_configure": (_I, [_VP, _I, _I]),
+    "pb_batch_solve": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I64), ctypes.POINTER(_I),
+                            ctypes.POINTER(_Opts), _I, ctypes.POINTER(_D), ctypes.POINTER(_BatchInfo)]),
     "pb_matvec_get_config": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64)]),
     "pb_matvec_autotune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
 }
@@ -293,6 +302,42 @@ def pb_matvec_autotune(ctx: Context, reps: int = 3) -> dict:
     v, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(lib().pb_matvec_autotune(ctx.handle, int(reps), ctypes.byref(v), ctypes.byref(c), ctypes.byref(ms)), ctx)
     return {"variant": v.value, "ctas_per_sm": c.value, "ms": ms.value}
+
+
+def pb_batch_solve(ctxs, charge_sets, restart: int = 10, tol: float = 1e-4, maxit: int = 1000,
+                   use_graph: bool = True, raise_on_noconv: bool = True):
+    """Solve every (surface, charge set) pair in lockstep.  ``ctxs``: list of
+    contexts; ``charge_sets[s]``: array (R_s, Nc_s, 4) or (Nc_s, 4) of host
+    charges.  Returns (energies as a list of R_s-length lists, info dict)."""
+    n = len(ctxs)
+    keep = []
+    handles = (ctypes.c_void_p * n)(*[c.handle for c in ctxs])
+    ptrs = (ctypes.c_void_p * n)()
+    ncs = (ctypes.c_int64 * n)()
+    nr = (ctypes.c_int * n)()
+    for i, q in enumerate(charge_sets):
+        a = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+        if a.ndim == 2:
+            a = a[None]
+        keep.append(a)
+        nr[i] = a.shape[0]
+        ncs[i] = a.shape[1]
+        ptrs[i] = a.ctypes.data if a.size else None
+    total = sum(nr)
+    en = (ctypes.c_double * total)()
+    o = _Opts(int(restart), float(tol), int(maxit), PB_FP32PAIR, 0)
+    info = _BatchInfo()
+    st = lib().pb_batch_solve(handles, n, ptrs, ncs, nr, ctypes.byref(o), 1 if use_graph else 0, en,
+                              ctypes.byref(info))
+    if st != PB_OK and not (st == PB_ERR_NOCONV and not raise_on_noconv):
+        _check(st, ctxs[0])
+    out, k = [], 0
+    for i in range(n):
+        out.append([en[k + r] for r in range(nr[i])])
+        k += nr[i]
+    d = {f: getattr(info, f) for f, _ in _BatchInfo._fields_}
+    d["status"] = st
+    return out, d
 
 
 def pb_destroy(ctx: Context) -> None:

@@ -15,6 +15,7 @@ static std::atomic<uint64_t> g_launches{0};
 static thread_local char g_thread_error[512];
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 pb_status set_error(pb_ctx *ctx, pb_status s, const char *fmt, ...) {
     char *buf = ctx ? ctx->last_error : g_thread_error;

@@ -159,6 +159,7 @@ namespace pb {
 pb_status set_error(pb_ctx *ctx, pb_status s, const char *fmt, ...);
 pb_status cuda_error(pb_ctx *ctx, cudaError_t e, const char *what);
 void count_launch();
+void count_launches(int n);
 #define PB_LAUNCHED() ::pb::count_launch()
 
 // allocation on the context's stream (stream-ordered pool)

@@ -1,0 +1,84 @@
+"""Batched lockstep solves (many surfaces of uneven N, several charge sets
+each): every batched energy equals the one-at-a-time solve of the same
+(surface, charge set) within the FP32-pair tolerance, and meets the 1e-5 bound
+against the FP64 oracle where the oracle is cheap enough."""
+import numpy as np
+import pytest
+
+import oracle
+import pb_inputs as pi
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import importlib
+    importlib.import_module("paper_1301_5885_gb300.build").build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _pb():
+    import paper_1301_5885_gb300 as pb
+    return pb
+
+
+def _mix():
+    """Uneven surfaces, 1..8 charge sets each, kappa in {0, 0.1257}."""
+    out = []
+    for k, (lvl, rad, nq, nr, kap) in enumerate([(2, 3.0, 3, 1, 0.1257), (3, 5.0, 6, 4, 0.0),
+                                                (4, 8.0, 10, 8, 0.1257), (3, 6.0, 5, 3, 0.1257)]):
+        p = pi.kirkwood_sphere_multi(level=lvl, radius=rad, n_charges=nq, seed=30 + k, kappa=kap)
+        sets = pi.charge_variants(p.charges, nr, seed=40 + k, frac=0.3)
+        out.append((p, sets))
+    sol = pi.protein_like(n_atoms=12, seed=6, target_triangles=None, spacing=1.4)
+    out.append((sol, pi.charge_variants(sol.charges, 2, seed=7, frac=0.2)))
+    return out
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batched_energies_match_single_solves(use_graph):
+    pb = _pb()
+    mix = _mix()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctxs = [pb.pb_create(p.surface.centroids, p.surface.normals, p.surface.areas, sets[0], p.eps1, p.eps2,
+                             p.kappa, stream=stream) for p, sets in mix]
+        energies, info = pb.pb_batch_solve(ctxs, [sets for _, sets in mix], tol=1e-7, maxit=2000,
+                                           use_graph=use_graph)
+        assert info["instances"] == sum(len(s) for _, s in mix) == info["converged"]
+        assert info["rhs_width"] == 8 and info["pair_products"] >= info["pair_evals"] > 0
+        for (p, sets), ctx, es in zip(mix, ctxs, energies):
+            assert len(es) == len(sets)
+            for r, q in enumerate(sets):
+                pb.pb_set_charges(ctx, q)
+                single = pb.pb_solve(ctx, tol=1e-7, maxit=2000, prec="fp32pair").energy_kcal
+                assert es[r] == pytest.approx(single, rel=2e-6, abs=1e-9)
+        for c in ctxs:
+            pb.pb_destroy(c)
+
+
+def test_batched_energies_meet_the_bound_against_the_oracle():
+    pb = _pb()
+    p = pi.kirkwood_sphere_multi(level=3, radius=6.0, n_charges=8, seed=51)
+    sets = pi.charge_variants(p.charges, 8, seed=52, frac=0.25)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = pb.pb_create(p.surface.centroids, p.surface.normals, p.surface.areas, sets[0], p.eps1, p.eps2,
+                           p.kappa, stream=stream)
+        energies, info = pb.pb_batch_solve([ctx], [sets], tol=1e-7)
+        pb.pb_destroy(ctx)
+    for r, q in enumerate(sets):
+        ref = oracle.solve(p.surface, q, p.eps1, p.eps2, p.kappa, tol=1e-11)["energy"]
+        assert energies[0][r] == pytest.approx(ref, rel=1e-5)
+
+
+def test_batch_rejects_bad_arguments():
+    pb = _pb()
+    p = pi.kirkwood_sphere_multi(level=2, radius=3.0, n_charges=2, seed=1)
+    with pb.pb_create(p.surface.centroids, p.surface.normals, p.surface.areas, p.charges, 1.0, 80.0, 0.1) as ctx:
+        with pytest.raises(pb.PBError):
+            pb.pb_batch_solve([ctx], [np.repeat(p.charges[None], 9, axis=0)])   # more than 8 charge sets
