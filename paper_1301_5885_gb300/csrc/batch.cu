@@ -10,35 +10,36 @@
 // the CTAs, and each pair's kernels K1..K4 (Eq. (10)) are evaluated once and
 // applied to all R right-hand sides of that surface (Eqs. (12)-(13)).  The
 // vector work of GMRES (Gram-Schmidt, norms, Givens, updates) runs in batched
-// kernels over a flat concatenation of all instance vectors, cut into chunks
-// that never straddle two instances; per-instance sums are fixed-order
-// two-stage reductions finished by the last chunk to arrive.  Instances that
-// have converged are skipped, and a surface whose instances are all idle is
-// skipped by the product.  One restart cycle of the whole batch can be
-// captured in a CUDA graph and replayed.
+// kernels over every instance's vectors, cut into chunks that never straddle
+// two instances; per-instance sums are fixed-order two-stage reductions
+// finished by the last chunk to arrive.  Instances that have converged are
+// skipped, and a surface whose instances are all idle is skipped by the
+// product.  Instances can join and leave between restart cycles (the solve
+// server relies on this); with a fixed set, one restart cycle of the whole
+// batch can be captured in a CUDA graph and replayed.
 #include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <vector>
 
+#include "engine.cuh"
 #include "fastmath.cuh"
 #include "pb_internal.cuh"
 #include "reduce.cuh"
 
 namespace pb {
-namespace {
 
 constexpr int kBThreads = 128;          // product kernel: one target per thread
 constexpr int kBSourceTile = 128;
 constexpr int kChunk = 4096;            // vector chunk (elements) of the GMRES kernels
 constexpr int kVThreads = 256;
-constexpr int kMaxRhs = 8;
 constexpr int LDH = kMaxRestart + 1;
 
 struct BSurf {
     const float4 *pos;
     const float4 *nrm;
-    const double *g64;     // FP64 SoA geometry (source term)
     int64_t N;
     float eps, inv_eps, kappa, nk;
     double diag1, diag2;
@@ -50,25 +51,20 @@ struct BSurf {
 };
 
 struct BInst {
-    int64_t off;           // offset of the instance's 2N-vector in the flat arrays
-    int64_t n;             // N of its surface
+    double *b, *x, *w, *r, *V;   // V: (m+1) vectors of 2N
+    GmresState *st;
+    int64_t n2;
     int surf;
-    int chunk0, nchunk;    // its chunks of the flat 2N vectors
-    int schunk0, nschunk;  // its chunks over the N sources (energy)
-    int64_t qoff;          // first charge
-    int64_t nc;
+    int chunk0, nchunk;          // its chunks of the 2N vectors
 };
 
 struct BChunk {
     int inst;
     int len;
-    int64_t start;         // flat index (vector chunks) or source index (source chunks)
+    int64_t start;               // relative to the instance's vectors
 };
 
-struct BStatus {
-    int done, converged, status, iters, cycles, pad;
-    double rel_resid;
-};
+namespace {
 
 __device__ __forceinline__ int vol(const int *p) { return *((volatile const int *)p); }
 
@@ -92,16 +88,18 @@ __device__ __forceinline__ int find_surface(const BSurf *surf, int nsurf, int64_
     return lo;
 }
 
+// y_q = A u_q for every instance q; u_q = x_q (usel 0) or V_q[k] (usel 1), y_q = w_q.
 template <int R>
 __global__ void __launch_bounds__(kBThreads)
 bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restrict__ inst, int64_t W, int64_t G,
-               const double *__restrict__ u, double *__restrict__ y, const int *__restrict__ active,
-               double *__restrict__ partials, unsigned int *__restrict__ counters,
-               unsigned long long *__restrict__ evaluated) {
-    constexpr int BS = kBThreads, TT = kBThreads, TS = kBSourceTile;
+               int usel, int k, const int *__restrict__ active, double *__restrict__ partials,
+               unsigned int *__restrict__ counters, unsigned long long *__restrict__ evaluated) {
+    constexpr int TT = kBThreads, TS = kBSourceTile;
     __shared__ float4 s_pos[TS];
     __shared__ float4 s_nrm[TS];
     __shared__ float2 s_w[R][TS];        // (W dphi, W phi) / (4 pi) per right-hand side
+    __shared__ const double *s_u[R];
+    __shared__ double *s_y[R];
     __shared__ int s_last;
     const int tid = threadIdx.x;
     const int64_t c = blockIdx.x;
@@ -128,7 +126,18 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
             continue;
         }
         if (local == 0 && tid == 0) atomicAdd(evaluated + si, 1ull);   // one product of this surface
-        int64_t i = a * TT + tid;
+        __syncthreads();                  // the previous segment is done with s_u / s_y
+        if (tid < R) {
+            if (tid < sf.nrhs) {
+                const BInst in = inst[sf.inst0 + tid];
+                s_u[tid] = usel ? in.V + (int64_t)k * in.n2 : in.x;
+                s_y[tid] = in.w;
+            } else {
+                s_u[tid] = nullptr;
+                s_y[tid] = nullptr;
+            }
+        }
+        const int64_t i = a * TT + tid;
         const int64_t ic = i < N ? i : N - 1;
         const float4 qi = sf.pos[ic], ni = sf.nrm[ic];
         double acc1[R], acc2[R];
@@ -145,12 +154,8 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
                     s_nrm[tid] = n;
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
-                        if (r < sf.nrhs) {
-                            const int64_t off = inst[sf.inst0 + r].off;
-                            s_w[r][tid] = make_float2((float)u[off + N + j] * q.w, (float)u[off + j] * q.w);
-                        } else {
-                            s_w[r][tid] = make_float2(0.f, 0.f);
-                        }
+                        const double *u = s_u[r];
+                        s_w[r][tid] = u ? make_float2((float)u[N + j] * q.w, (float)u[j] * q.w) : make_float2(0.f, 0.f);
                     }
                 }
             }
@@ -199,10 +204,9 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
             if (i < N) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    if (r < sf.nrhs) {
-                        const int64_t off = inst[sf.inst0 + r].off;
-                        y[off + i] = sf.diag1 * u[off + i] - acc1[r];
-                        y[off + N + i] = sf.diag2 * u[off + N + i] - acc2[r];
+                    if (s_y[r]) {
+                        s_y[r][i] = sf.diag1 * s_u[r][i] - acc1[r];
+                        s_y[r][N + i] = sf.diag2 * s_u[r][N + i] - acc2[r];
                     }
                 }
             }
@@ -238,10 +242,9 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
                 if (i < N) {
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
-                        if (r < sf.nrhs) {
-                            const int64_t off = inst[sf.inst0 + r].off;
-                            y[off + i] = sf.diag1 * u[off + i] - s1[r];
-                            y[off + N + i] = sf.diag2 * u[off + N + i] - s2[r];
+                        if (s_y[r]) {
+                            s_y[r][i] = sf.diag1 * s_u[r][i] - s1[r];
+                            s_y[r][N + i] = sf.diag2 * s_u[r][N + i] - s2[r];
                         }
                     }
                 }
@@ -254,43 +257,25 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
 
 // ---- batched GMRES vector kernels (one block per chunk) ----------------------
 __global__ void __launch_bounds__(kVThreads)
-bg_norm(const double *__restrict__ v, const BChunk *__restrict__ ch, const BInst *__restrict__ inst,
-        double *__restrict__ red, unsigned int *__restrict__ counters, GmresState *st) {
+bg_cycle_start(int usex, const BChunk *__restrict__ ch, const BInst *__restrict__ inst, double *__restrict__ red,
+               unsigned int *__restrict__ counters) {
     const BChunk c = ch[blockIdx.x];
-    double s = 0.0;
-    for (int k = threadIdx.x; k < c.len; k += kVThreads) { const double t = v[c.start + k]; s += t * t; }
-    s = block_sum<kVThreads>(s);
-    if (threadIdx.x == 0) red[blockIdx.x] = s;
-    const BInst q = inst[c.inst];
-    if (inst_last(&counters[c.inst], q.nchunk) && threadIdx.x == 0) {
-        double t = 0.0;
-        for (int b = 0; b < q.nchunk; ++b) t += __ldcg(red + q.chunk0 + b);
-        st[c.inst].bnorm = sqrt(t);
-        counters[c.inst] = 0u;
-    }
-}
-
-__global__ void __launch_bounds__(kVThreads)
-bg_cycle_start(const double *__restrict__ rhs, const double *__restrict__ Ax, double *__restrict__ r,
-               const BChunk *__restrict__ ch, const BInst *__restrict__ inst, double *__restrict__ red,
-               unsigned int *__restrict__ counters, GmresState *st) {
-    const BChunk c = ch[blockIdx.x];
-    GmresState *g = st + c.inst;
+    const BInst in = inst[c.inst];
+    GmresState *g = in.st;
     if (vol(&g->done)) return;
-    const bool zero = vol(&g->x_is_zero) != 0;
+    const bool zero = vol(&g->x_is_zero) != 0 || !usex;
     double s = 0.0;
     for (int k = threadIdx.x; k < c.len; k += kVThreads) {
         const int64_t e = c.start + k;
-        const double ri = zero ? rhs[e] : rhs[e] - Ax[e];
-        r[e] = ri;
+        const double ri = zero ? in.b[e] : in.b[e] - in.w[e];
+        in.r[e] = ri;
         s += ri * ri;
     }
     s = block_sum<kVThreads>(s);
     if (threadIdx.x == 0) red[blockIdx.x] = s;
-    const BInst q = inst[c.inst];
-    if (inst_last(&counters[c.inst], q.nchunk) && threadIdx.x == 0) {
+    if (inst_last(&counters[c.inst], in.nchunk) && threadIdx.x == 0) {
         double t = 0.0;
-        for (int b = 0; b < q.nchunk; ++b) t += __ldcg(red + q.chunk0 + b);
+        for (int b = 0; b < in.nchunk; ++b) t += __ldcg(red + in.chunk0 + b);
         counters[c.inst] = 0u;
         const double beta = sqrt(t);
         g->k = 0;
@@ -317,34 +302,36 @@ bg_cycle_start(const double *__restrict__ rhs, const double *__restrict__ Ax, do
     }
 }
 
+// V[0] = r / beta (which = 0) or V[k+1] = w / H[k+1,k] (which = 1)
 __global__ void __launch_bounds__(kVThreads)
-bg_scale(const double *__restrict__ src, double *__restrict__ dst, const BChunk *__restrict__ ch,
-         const GmresState *st, int which) {
+bg_scale(int which, int k, const BChunk *__restrict__ ch, const BInst *__restrict__ inst) {
     const BChunk c = ch[blockIdx.x];
-    const GmresState *g = st + c.inst;
+    const BInst in = inst[c.inst];
+    const GmresState *g = in.st;
     if (vol(&g->skip)) return;
+    const double *src = which ? in.w : in.r;
+    double *dst = in.V + (which ? (int64_t)(k + 1) * in.n2 : 0);
     const double inv = 1.0 / (which ? g->hnext : g->beta);
-    for (int k = threadIdx.x; k < c.len; k += kVThreads) dst[c.start + k] = src[c.start + k] * inv;
+    for (int e = threadIdx.x; e < c.len; e += kVThreads) dst[c.start + e] = src[c.start + e] * inv;
 }
 
 __global__ void __launch_bounds__(kVThreads)
-bg_dots(const double *__restrict__ V, int64_t L, const double *__restrict__ w, int k, const BChunk *__restrict__ ch,
-        const BInst *__restrict__ inst, double *__restrict__ red, int nchunks, unsigned int *__restrict__ counters,
-        GmresState *st) {
+bg_dots(int k, const BChunk *__restrict__ ch, const BInst *__restrict__ inst, double *__restrict__ red, int nchunks,
+        unsigned int *__restrict__ counters) {
     const BChunk c = ch[blockIdx.x];
-    GmresState *g = st + c.inst;
+    const BInst in = inst[c.inst];
+    GmresState *g = in.st;
     if (vol(&g->skip)) return;
     const int v = blockIdx.y;
-    const double *Vv = V + (int64_t)v * L;
+    const double *Vv = in.V + (int64_t)v * in.n2;
     double s = 0.0;
-    for (int e = threadIdx.x; e < c.len; e += kVThreads) s += Vv[c.start + e] * w[c.start + e];
+    for (int e = threadIdx.x; e < c.len; e += kVThreads) s += Vv[c.start + e] * in.w[c.start + e];
     s = block_sum<kVThreads>(s);
     if (threadIdx.x == 0) red[(int64_t)v * nchunks + blockIdx.x] = s;
-    const BInst q = inst[c.inst];
-    if (inst_last(&counters[c.inst], q.nchunk * (k + 1))) {
+    if (inst_last(&counters[c.inst], in.nchunk * (k + 1))) {
         for (int vv = threadIdx.x; vv <= k; vv += kVThreads) {
             double t = 0.0;
-            for (int b = 0; b < q.nchunk; ++b) t += __ldcg(red + (int64_t)vv * nchunks + q.chunk0 + b);
+            for (int b = 0; b < in.nchunk; ++b) t += __ldcg(red + (int64_t)vv * nchunks + in.chunk0 + b);
             g->h1[vv] = t;
         }
         if (threadIdx.x == 0) counters[c.inst] = 0u;
@@ -352,32 +339,32 @@ bg_dots(const double *__restrict__ V, int64_t L, const double *__restrict__ w, i
 }
 
 __global__ void __launch_bounds__(kVThreads)
-bg_orth1(const double *__restrict__ V, int64_t L, double *__restrict__ w, int k, const BChunk *__restrict__ ch,
-         const BInst *__restrict__ inst, double *__restrict__ red, int nchunks, unsigned int *__restrict__ counters,
-         GmresState *st) {
+bg_orth1(int k, const BChunk *__restrict__ ch, const BInst *__restrict__ inst, double *__restrict__ red, int nchunks,
+         unsigned int *__restrict__ counters) {
     const BChunk c = ch[blockIdx.x];
-    GmresState *g = st + c.inst;
+    const BInst in = inst[c.inst];
+    GmresState *g = in.st;
     if (vol(&g->skip)) return;
     __shared__ double s_h[LDH];
     for (int v = threadIdx.x; v <= k; v += kVThreads) s_h[v] = g->h1[v];
     __syncthreads();
     for (int e = threadIdx.x; e < c.len; e += kVThreads) {
         const int64_t x = c.start + e;
-        double wi = w[x];
-        for (int v = 0; v <= k; ++v) wi -= s_h[v] * V[(int64_t)v * L + x];
-        w[x] = wi;
+        double wi = in.w[x];
+        for (int v = 0; v <= k; ++v) wi -= s_h[v] * in.V[(int64_t)v * in.n2 + x];
+        in.w[x] = wi;
     }
     for (int v = 0; v <= k; ++v) {
         double s = 0.0;
-        for (int e = threadIdx.x; e < c.len; e += kVThreads) s += V[(int64_t)v * L + c.start + e] * w[c.start + e];
+        for (int e = threadIdx.x; e < c.len; e += kVThreads)
+            s += in.V[(int64_t)v * in.n2 + c.start + e] * in.w[c.start + e];
         s = block_sum<kVThreads>(s);
         if (threadIdx.x == 0) red[(int64_t)v * nchunks + blockIdx.x] = s;
     }
-    const BInst q = inst[c.inst];
-    if (inst_last(&counters[c.inst], q.nchunk)) {
+    if (inst_last(&counters[c.inst], in.nchunk)) {
         for (int vv = threadIdx.x; vv <= k; vv += kVThreads) {
             double t = 0.0;
-            for (int b = 0; b < q.nchunk; ++b) t += __ldcg(red + (int64_t)vv * nchunks + q.chunk0 + b);
+            for (int b = 0; b < in.nchunk; ++b) t += __ldcg(red + (int64_t)vv * nchunks + in.chunk0 + b);
             g->h2[vv] = t;
         }
         if (threadIdx.x == 0) counters[c.inst] = 0u;
@@ -385,10 +372,11 @@ bg_orth1(const double *__restrict__ V, int64_t L, double *__restrict__ w, int k,
 }
 
 __global__ void __launch_bounds__(kVThreads)
-bg_orth2(const double *__restrict__ V, int64_t L, double *__restrict__ w, int k, const BChunk *__restrict__ ch,
-         const BInst *__restrict__ inst, double *__restrict__ red, unsigned int *__restrict__ counters, GmresState *st) {
+bg_orth2(int k, const BChunk *__restrict__ ch, const BInst *__restrict__ inst, double *__restrict__ red,
+         unsigned int *__restrict__ counters) {
     const BChunk c = ch[blockIdx.x];
-    GmresState *g = st + c.inst;
+    const BInst in = inst[c.inst];
+    GmresState *g = in.st;
     if (vol(&g->skip)) return;
     __shared__ double s_h[LDH];
     for (int v = threadIdx.x; v <= k; v += kVThreads) s_h[v] = g->h2[v];
@@ -396,17 +384,16 @@ bg_orth2(const double *__restrict__ V, int64_t L, double *__restrict__ w, int k,
     double s = 0.0;
     for (int e = threadIdx.x; e < c.len; e += kVThreads) {
         const int64_t x = c.start + e;
-        double wi = w[x];
-        for (int v = 0; v <= k; ++v) wi -= s_h[v] * V[(int64_t)v * L + x];
-        w[x] = wi;
+        double wi = in.w[x];
+        for (int v = 0; v <= k; ++v) wi -= s_h[v] * in.V[(int64_t)v * in.n2 + x];
+        in.w[x] = wi;
         s += wi * wi;
     }
     s = block_sum<kVThreads>(s);
     if (threadIdx.x == 0) red[blockIdx.x] = s;
-    const BInst q = inst[c.inst];
-    if (inst_last(&counters[c.inst], q.nchunk) && threadIdx.x == 0) {
+    if (inst_last(&counters[c.inst], in.nchunk) && threadIdx.x == 0) {
         double t = 0.0;
-        for (int b = 0; b < q.nchunk; ++b) t += __ldcg(red + q.chunk0 + b);
+        for (int b = 0; b < in.nchunk; ++b) t += __ldcg(red + in.chunk0 + b);
         counters[c.inst] = 0u;
         const double hn = sqrt(t);
         double *H = g->H;
@@ -440,48 +427,44 @@ bg_orth2(const double *__restrict__ V, int64_t L, double *__restrict__ w, int k,
     }
 }
 
-__global__ void bg_trisolve(GmresState *st, int nq) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nq) return;
-    GmresState *g = st + q;
-    const int kk = g->k;
-    if (kk == 0 || g->status != PB_OK) return;
-    const double *H = g->H;
-    for (int i = kk - 1; i >= 0; --i) {
-        double t = g->g[i];
-        for (int j = i + 1; j < kk; ++j) t -= H[i + j * LDH] * g->y[j];
-        g->y[i] = t / H[i + i * LDH];
-    }
-}
-
+// back substitution and x += V y, one block per chunk (block 0 of an instance
+// solves the small triangular system into shared memory; every block redoes
+// it, which is cheaper than another launch for k <= 64)
 __global__ void __launch_bounds__(kVThreads)
-bg_update_x(const double *__restrict__ V, int64_t L, double *__restrict__ x, const BChunk *__restrict__ ch,
-            GmresState *st) {
+bg_update_x(const BChunk *__restrict__ ch, const BInst *__restrict__ inst) {
     const BChunk c = ch[blockIdx.x];
-    GmresState *g = st + c.inst;
+    const BInst in = inst[c.inst];
+    const GmresState *g = in.st;
     const int kk = g->k;
     if (kk == 0 || g->status != PB_OK || vol(&g->done)) return;
     __shared__ double s_y[kMaxRestart];
-    for (int v = threadIdx.x; v < kk; v += kVThreads) s_y[v] = g->y[v];
+    if (threadIdx.x == 0) {
+        const double *H = g->H;
+        for (int i = kk - 1; i >= 0; --i) {
+            double t = g->g[i];
+            for (int j = i + 1; j < kk; ++j) t -= H[i + j * LDH] * s_y[j];
+            s_y[i] = t / H[i + i * LDH];
+        }
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < c.len; e += kVThreads) {
         const int64_t xi = c.start + e;
-        double t = x[xi];
-        for (int v = 0; v < kk; ++v) t += s_y[v] * V[(int64_t)v * L + xi];
-        x[xi] = t;
+        double t = in.x[xi];
+        for (int v = 0; v < kk; ++v) t += s_y[v] * in.V[(int64_t)v * in.n2 + xi];
+        in.x[xi] = t;
     }
 }
 
 // per-surface activity flags for the product, and x_is_zero bookkeeping
-__global__ void bg_flags(const BSurf *__restrict__ surf, int nsurf, GmresState *st, int *act_step, int *act_ax,
-                         int clear_x_zero) {
+__global__ void bg_flags(const BSurf *__restrict__ surf, int nsurf, const BInst *__restrict__ inst, int *act_step,
+                         int *act_ax, int clear_x_zero) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsurf) return;
     const BSurf sf = surf[s];
     int step = 0, ax = 0;
     for (int r = 0; r < sf.nrhs; ++r) {
-        GmresState *g = st + sf.inst0 + r;
-        if (clear_x_zero && g->k > 0) g->x_is_zero = 0;
+        GmresState *g = inst[sf.inst0 + r].st;
+        if (clear_x_zero && g->k > 0 && g->status == PB_OK) g->x_is_zero = 0;
         step |= !g->skip;
         ax |= (!g->done && !g->x_is_zero);
     }
@@ -489,79 +472,409 @@ __global__ void bg_flags(const BSurf *__restrict__ surf, int nsurf, GmresState *
     act_ax[s] = ax;
 }
 
-__global__ void bg_status(const GmresState *st, int nq, BStatus *out) {
+__global__ void bg_status(const BInst *__restrict__ inst, int nq, BStatus *out) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
-    const GmresState *g = st + q;
+    const GmresState *g = inst[q].st;
     out[q] = BStatus{g->done, g->converged, g->status, g->iters, g->cycles, 0, g->rel_resid};
 }
 
-__global__ void bg_init(GmresState *st, int nq, int m, int maxit, double tol) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nq) return;
-    GmresState *g = st + q;
-    g->m = m;
-    g->maxit = maxit;
-    g->tol = tol;
-    g->k = 0;
-    g->iters = 0;
-    g->cycles = 0;
-    g->cycle_done = 0;
-    g->done = 0;
-    g->skip = 0;
-    g->converged = 0;
-    g->status = PB_OK;
-    g->x_is_zero = 1;
-    g->bnorm = 0.0;
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Engine
+// ---------------------------------------------------------------------------
+Engine::Engine(cudaStream_t stream, int device, int num_sms, int m, double tol, int maxit)
+    : stream_(stream), device_(device), num_sms_(num_sms), m_(m), maxit_(maxit), tol_(tol) {}
+
+Engine::~Engine() {
+    for (EngineMember *mb : members_) {
+        cudaFreeAsync(mb->q, stream_);
+        cudaFreeAsync(mb->vec, stream_);
+        cudaFreeAsync(mb->st, stream_);
+        delete mb;
+    }
+    void *bufs[] = {d_surf_, d_inst_, d_ch_, cnt_inst_, cnt_tile_, evals_, act_step_, act_ax_, red_, part_, scalar_,
+                    d_status_};
+    for (void *p : bufs)
+        if (p) cudaFreeAsync(p, stream_);
+    if (gexec_) cudaGraphExecDestroy(gexec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    cudaStreamSynchronize(stream_);
+    if (h_status_) cudaFreeHost(h_status_);
 }
 
-// b = [S1; S2] (Eq. (11)) for every instance; one block per source chunk of 256 targets
-__global__ void __launch_bounds__(kVThreads)
-bg_source(const BChunk *__restrict__ sch, const BInst *__restrict__ inst, const BSurf *__restrict__ surf,
-          const Charge4 *__restrict__ q, const double *__restrict__ inv_eps1, double *__restrict__ b) {
-    const BChunk c = sch[blockIdx.x];
-    const BInst in = inst[c.inst];
-    const BSurf sf = surf[in.surf];
-    const int64_t N = sf.N;
-    const int64_t i = c.start + threadIdx.x;
-    const bool on = threadIdx.x < c.len;
-    const int64_t ic = on ? i : c.start;
-    const double px = sf.g64[ic], py = sf.g64[N + ic], pz = sf.g64[2 * N + ic];
-    const double nx = sf.g64[3 * N + ic], ny = sf.g64[4 * N + ic], nz = sf.g64[5 * N + ic];
-    double s1 = 0.0, s2 = 0.0;
-    for (int64_t k = 0; k < in.nc; ++k) {
-        const Charge4 ch = q[in.qoff + k];
-        const double dx = px - ch.x, dy = py - ch.y, dz = pz - ch.z;
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 > 0.0) {
-            const double inv = rsqrt(r2);
-            s1 += ch.q * inv;
-            s2 -= ch.q * (dx * nx + dy * ny + dz * nz) * inv * inv * inv;
+pb_status Engine::fail(pb_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(error, sizeof(error), fmt, ap);
+    va_end(ap);
+    return set_error(nullptr, s, "%s", error);
+}
+
+pb_status Engine::cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? PB_ERR_OOM : PB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+pb_status Engine::grow(void **p, size_t *cap, size_t need, size_t elem, const char *what) {
+    if (need <= *cap && *p) return PB_OK;
+    if (*p) cudaFreeAsync(*p, stream_);
+    *p = nullptr;
+    size_t n = need < 16 ? 16 : need + need / 2;
+    cudaError_t e = cudaMallocAsync(p, n * elem, stream_);
+    if (e != cudaSuccess) {
+        *cap = 0;
+        *p = nullptr;
+        return cuda_fail(e, what);
+    }
+    *cap = n;
+    return PB_OK;
+}
+
+int64_t Engine::member_bytes(int64_t N, int nrhs, int m) {
+    return (int64_t)nrhs * ((int64_t)(m + 5) * 2 * N * (int64_t)sizeof(double) + (int64_t)sizeof(GmresState));
+}
+
+EngineMember *Engine::add(pb_ctx *surf, const double *charges_host, int64_t nc, int nrhs, uint64_t tag,
+                          pb_status *st) {
+    *st = PB_OK;
+    if (!surf || nrhs < 1 || nrhs > kEngineMaxRhs || nc < 0 || (nc > 0 && !charges_host)) {
+        *st = fail(PB_ERR_ARG, "engine: bad member arguments");
+        return nullptr;
+    }
+    EngineMember *mb = new EngineMember();
+    mb->surf = surf;
+    mb->nrhs = nrhs;
+    mb->nc = nc;
+    mb->tag = tag;
+    const int64_t n2 = 2 * surf->N;
+    const size_t per = (size_t)(m_ + 5) * n2;
+    cudaError_t e = cudaMallocAsync((void **)&mb->vec, per * nrhs * sizeof(double), stream_);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&mb->st, nrhs * sizeof(GmresState), stream_);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&mb->q, (nc > 0 ? nc * nrhs : 1) * sizeof(Charge4), stream_);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (mb->vec) cudaFreeAsync(mb->vec, stream_);
+        if (mb->st) cudaFreeAsync(mb->st, stream_);
+        if (mb->q) cudaFreeAsync(mb->q, stream_);
+        delete mb;
+        *st = cuda_fail(e, "engine member allocation");
+        return nullptr;
+    }
+    mb->bytes = member_bytes(surf->N, nrhs, m_) + nc * nrhs * (int64_t)sizeof(Charge4);
+    // charges, centred like the surface's geometry
+    std::vector<Charge4> hq((size_t)(nc * nrhs));
+    for (int64_t k = 0; k < nc * nrhs; ++k)
+        hq[k] = Charge4{charges_host[4 * k] - surf->center[0], charges_host[4 * k + 1] - surf->center[1],
+                        charges_host[4 * k + 2] - surf->center[2], charges_host[4 * k + 3]};
+    if (nc > 0) e = cudaMemcpyAsync(mb->q, hq.data(), hq.size() * sizeof(Charge4), cudaMemcpyHostToDevice, stream_);
+    // initial states (x0 = 0)
+    GmresState init;
+    memset(&init, 0, sizeof(init));
+    init.m = m_;
+    init.maxit = maxit_;
+    init.tol = tol_;
+    init.status = PB_OK;
+    init.x_is_zero = 1;
+    for (int r = 0; r < nrhs && e == cudaSuccess; ++r)
+        e = cudaMemcpyAsync(mb->st + r, &init, sizeof(init), cudaMemcpyHostToDevice, stream_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mb->vec, 0, per * nrhs * sizeof(double), stream_);
+    // the host staging vector goes out of scope: finish the copies first
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    // b = [S1; S2] and ||b|| for every set, through the context's FP64 kernels
+    Charge4 *keep_q = surf->charges;
+    const int64_t keep_nc = surf->Nc;
+    const cudaStream_t keep_stream = surf->stream;
+    surf->stream = stream_;
+    for (int r = 0; r < nrhs && e == cudaSuccess && *st == PB_OK; ++r) {
+        double *b = mb->vec + (size_t)r * per;
+        surf->charges = mb->q + r * nc;
+        surf->Nc = nc;
+        *st = source_launch(surf, b, PB_FP64);
+        if (*st == PB_OK) *st = norm2_launch(surf, b, n2, &mb->st[r].bnorm);
+    }
+    surf->charges = keep_q;
+    surf->Nc = keep_nc;
+    surf->stream = keep_stream;
+    if (e != cudaSuccess && *st == PB_OK) *st = cuda_fail(e, "engine member initialisation");
+    if (*st != PB_OK) {
+        cudaFreeAsync(mb->vec, stream_);
+        cudaFreeAsync(mb->st, stream_);
+        cudaFreeAsync(mb->q, stream_);
+        delete mb;
+        return nullptr;
+    }
+    members_.push_back(mb);
+    dirty_ = true;
+    return mb;
+}
+
+void Engine::remove(EngineMember *mb) {
+    for (size_t i = 0; i < members_.size(); ++i) {
+        if (members_[i] == mb) {
+            members_.erase(members_.begin() + i);
+            break;
         }
     }
-    if (on) {
-        const double sc = kInv4Pi * inv_eps1[in.surf];
-        b[in.off + i] = sc * s1;
-        b[in.off + in.n + i] = sc * s2;
-    }
+    cudaFreeAsync(mb->q, stream_);
+    cudaFreeAsync(mb->vec, stream_);
+    cudaFreeAsync(mb->st, stream_);
+    delete mb;
+    dirty_ = true;
 }
 
-}  // namespace
+pb_status Engine::rebuild() {
+    std::vector<BSurf> hs;
+    std::vector<BInst> hq;
+    std::vector<BChunk> hch;
+    surf_member_.clear();
+    int64_t tiles = 0, work = 0;
+    int rmax = 1;
+    for (size_t mi = 0; mi < members_.size(); ++mi) {
+        EngineMember *mb = members_[mi];
+        if (mb->finished) continue;
+        pb_ctx *c = mb->surf;
+        BSurf sf;
+        sf.pos = c->pos32;
+        sf.nrm = c->nrm32;
+        sf.N = c->N;
+        sf.eps = (float)c->eps;
+        sf.inv_eps = (float)(1.0 / c->eps);
+        sf.kappa = (float)c->kappa;
+        sf.nk = (float)(-c->kappa * 1.4426950408889634);
+        sf.diag1 = 0.5 * (1.0 + c->eps);
+        sf.diag2 = 0.5 * (1.0 + 1.0 / c->eps);
+        const int64_t T = (c->N + kBThreads - 1) / kBThreads;
+        sf.S = (c->N + kBSourceTile - 1) / kBSourceTile;
+        sf.tile_base = tiles;
+        sf.work_base = work;
+        sf.inst0 = (int)hq.size();
+        sf.nrhs = mb->nrhs;
+        tiles += T;
+        work += T * sf.S;
+        rmax = mb->nrhs > rmax ? mb->nrhs : rmax;
+        const int64_t n2 = 2 * c->N;
+        const size_t per = (size_t)(m_ + 5) * n2;
+        for (int r = 0; r < mb->nrhs; ++r) {
+            BInst in;
+            double *base = mb->vec + (size_t)r * per;
+            in.b = base;
+            in.x = base + n2;
+            in.w = base + 2 * n2;
+            in.r = base + 3 * n2;
+            in.V = base + 4 * n2;
+            in.st = mb->st + r;
+            in.n2 = n2;
+            in.surf = (int)hs.size();
+            in.chunk0 = (int)hch.size();
+            for (int64_t s0 = 0; s0 < n2; s0 += kChunk)
+                hch.push_back(BChunk{(int)hq.size(), (int)((n2 - s0) < kChunk ? (n2 - s0) : kChunk), s0});
+            in.nchunk = (int)hch.size() - in.chunk0;
+            hq.push_back(in);
+        }
+        hs.push_back(sf);
+        surf_member_.push_back((int)mi);
+    }
+    nsurf_ = (int)hs.size();
+    nq_ = (int)hq.size();
+    nchunks_ = (int)hch.size();
+    tiles_ = tiles;
+    W_ = work;
+    R_ = rmax <= 1 ? 1 : (rmax <= 2 ? 2 : (rmax <= 4 ? 4 : 8));
+    rhs_width = R_;
+    if (gexec_) cudaGraphExecDestroy(gexec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    gexec_ = nullptr;
+    graph_ = nullptr;
+    dirty_ = false;
+    if (nsurf_ == 0) return PB_OK;
+    int occ = 0;
+    switch (R_) {
+        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bmatvec_kernel<1>, kBThreads, 0); break;
+        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bmatvec_kernel<2>, kBThreads, 0); break;
+        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bmatvec_kernel<4>, kBThreads, 0); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bmatvec_kernel<8>, kBThreads, 0); break;
+    }
+    if (occ < 1) occ = 1;
+    G_ = (int64_t)num_sms_ * occ;
+    if (G_ > W_) G_ = W_;
+    ctas = G_;
+    pb_status s = PB_OK;
+    if (s == PB_OK) s = grow((void **)&d_surf_, &cap_surf_, nsurf_, sizeof(BSurf), "engine surfaces");
+    if (s == PB_OK) s = grow((void **)&d_inst_, &cap_inst_, nq_, sizeof(BInst), "engine instances");
+    if (s == PB_OK) s = grow((void **)&d_ch_, &cap_ch_, nchunks_, sizeof(BChunk), "engine chunks");
+    if (s == PB_OK) s = grow((void **)&cnt_inst_, &cap_cnt_inst_, nq_, sizeof(unsigned int), "engine counters");
+    if (s == PB_OK) s = grow((void **)&cnt_tile_, &cap_cnt_tile_, tiles_, sizeof(unsigned int), "engine counters");
+    if (s == PB_OK) s = grow((void **)&evals_, &cap_evals_, nsurf_, sizeof(unsigned long long), "engine counters");
+    if (s == PB_OK) s = grow((void **)&act_step_, &cap_flags_, nsurf_, sizeof(int), "engine flags");
+    if (s == PB_OK) {
+        size_t c2 = 0;
+        if (act_ax_) cudaFreeAsync(act_ax_, stream_);
+        act_ax_ = nullptr;
+        s = grow((void **)&act_ax_, &c2, cap_flags_, sizeof(int), "engine flags");
+    }
+    if (s == PB_OK) s = grow((void **)&red_, &cap_red_, (size_t)(m_ + 1) * nchunks_, sizeof(double), "engine reductions");
+    if (s == PB_OK) s = grow((void **)&part_, &cap_part_, (size_t)2 * G_ * 2 * R_ * kBThreads, sizeof(double), "engine partials");
+    if (s == PB_OK && !scalar_) {
+        cudaError_t e = cudaMallocAsync((void **)&scalar_, 64 * sizeof(double), stream_);
+        if (e != cudaSuccess) s = cuda_fail(e, "engine scalars");
+    }
+    if (s == PB_OK && cap_status_ < (size_t)nq_) {
+        if (d_status_) cudaFreeAsync(d_status_, stream_);
+        d_status_ = nullptr;
+        if (h_status_) {
+            cudaStreamSynchronize(stream_);
+            cudaFreeHost(h_status_);
+            h_status_ = nullptr;
+        }
+        size_t cap = 0;
+        s = grow((void **)&d_status_, &cap, nq_, sizeof(BStatus), "engine status");
+        if (s == PB_OK) {
+            cudaError_t e = cudaMallocHost((void **)&h_status_, cap * sizeof(BStatus));
+            if (e != cudaSuccess) s = cuda_fail(e, "engine pinned status");
+            else cap_status_ = cap;
+        }
+    }
+    if (s != PB_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(d_surf_, hs.data(), nsurf_ * sizeof(BSurf), cudaMemcpyHostToDevice, stream_);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_inst_, hq.data(), nq_ * sizeof(BInst), cudaMemcpyHostToDevice, stream_);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ch_, hch.data(), nchunks_ * sizeof(BChunk), cudaMemcpyHostToDevice, stream_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt_inst_, 0, nq_ * sizeof(unsigned int), stream_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt_tile_, 0, tiles_ * sizeof(unsigned int), stream_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(evals_, 0, nsurf_ * sizeof(unsigned long long), stream_);
+    // the staging vectors are pageable and local: wait for the copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    if (e != cudaSuccess) return cuda_fail(e, "engine table upload");
+    last_evals_.assign(nsurf_, 0ull);
+    // flags from the current states (members may be mid-solve)
+    bg_flags<<<(nsurf_ + 127) / 128, 128, 0, stream_>>>(d_surf_, nsurf_, d_inst_, act_step_, act_ax_, 0);
+    count_launch();
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PB_OK : cuda_fail(e, "engine flags");
+}
+
+void Engine::enqueue_cycle() {
+    const int sb = (nsurf_ + 127) / 128, qb = (nq_ + 127) / 128;
+    auto mv = [&](int usel, int k, const int *act) {
+        switch (R_) {
+            case 1: bmatvec_kernel<1><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
+            case 2: bmatvec_kernel<2><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
+            case 4: bmatvec_kernel<4><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
+            default: bmatvec_kernel<8><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
+        }
+        ++cycle_kernels_;
+        ++cycle_mv_;
+    };
+    mv(0, 0, act_ax_);
+    bg_cycle_start<<<nchunks_, kVThreads, 0, stream_>>>(1, d_ch_, d_inst_, red_, cnt_inst_);
+    bg_scale<<<nchunks_, kVThreads, 0, stream_>>>(0, 0, d_ch_, d_inst_);
+    bg_flags<<<sb, 128, 0, stream_>>>(d_surf_, nsurf_, d_inst_, act_step_, act_ax_, 0);
+    cycle_kernels_ += 3;
+    for (int k = 0; k < m_; ++k) {
+        mv(1, k, act_step_);
+        bg_dots<<<dim3(nchunks_, k + 1), kVThreads, 0, stream_>>>(k, d_ch_, d_inst_, red_, nchunks_, cnt_inst_);
+        bg_orth1<<<nchunks_, kVThreads, 0, stream_>>>(k, d_ch_, d_inst_, red_, nchunks_, cnt_inst_);
+        bg_orth2<<<nchunks_, kVThreads, 0, stream_>>>(k, d_ch_, d_inst_, red_, cnt_inst_);
+        bg_scale<<<nchunks_, kVThreads, 0, stream_>>>(1, k, d_ch_, d_inst_);
+        bg_flags<<<sb, 128, 0, stream_>>>(d_surf_, nsurf_, d_inst_, act_step_, act_ax_, 0);
+        cycle_kernels_ += 5;
+    }
+    bg_update_x<<<nchunks_, kVThreads, 0, stream_>>>(d_ch_, d_inst_);
+    bg_flags<<<sb, 128, 0, stream_>>>(d_surf_, nsurf_, d_inst_, act_step_, act_ax_, 1);
+    bg_status<<<qb, 128, 0, stream_>>>(d_inst_, nq_, d_status_);
+    cycle_kernels_ += 3;
+}
+
+pb_status Engine::cycle(bool use_graph) {
+    pb_status s = PB_OK;
+    if (dirty_ && (s = rebuild()) != PB_OK) return s;
+    if (nsurf_ == 0) return PB_OK;
+    cudaError_t e = cudaSuccess;
+    if (use_graph && stream_ != nullptr && !gexec_) {
+        cycle_kernels_ = 0;
+        cycle_mv_ = 0;
+        e = cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            enqueue_cycle();
+            cudaError_t e2 = cudaStreamEndCapture(stream_, &graph_);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec_, graph_, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "engine graph capture");
+        kernels_per_cycle_ = cycle_kernels_;
+        mv_per_cycle_ = cycle_mv_;
+    }
+    if (use_graph && gexec_) {
+        e = cudaGraphLaunch(gexec_, stream_);
+        count_launches(kernels_per_cycle_);
+        matvec_launches += mv_per_cycle_;
+    } else {
+        cycle_kernels_ = 0;
+        cycle_mv_ = 0;
+        enqueue_cycle();
+        count_launches(cycle_kernels_);
+        matvec_launches += cycle_mv_;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_status_, d_status_, nq_ * sizeof(BStatus), cudaMemcpyDeviceToHost, stream_);
+    std::vector<unsigned long long> ev(nsurf_, 0ull);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ev.data(), evals_, nsurf_ * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream_);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    if (e != cudaSuccess) return cuda_fail(e, "engine cycle");
+    ++cycles_run;
+    int q = 0;
+    for (int si = 0; si < nsurf_; ++si) {
+        EngineMember *mb = members_[surf_member_[si]];
+        const int64_t pairs = mb->surf->N * (mb->surf->N - 1);
+        pair_evals += (int64_t)(ev[si] - last_evals_[si]) * pairs;
+        pair_products += (int64_t)(ev[si] - last_evals_[si]) * pairs * mb->nrhs;
+        last_evals_[si] = ev[si];
+        bool all = true;
+        for (int r = 0; r < mb->nrhs; ++r, ++q) {
+            mb->status[r] = h_status_[q];
+            all &= h_status_[q].done != 0;
+        }
+        if (all && !mb->finished) {
+            mb->finished = true;
+        }
+    }
+    return PB_OK;
+}
+
+pb_status Engine::energies(EngineMember *mb, double *out) {
+    pb_ctx *c = mb->surf;
+    const int64_t n2 = 2 * c->N;
+    const size_t per = (size_t)(m_ + 5) * n2;
+    if (!scalar_) {
+        cudaError_t e = cudaMallocAsync((void **)&scalar_, 64 * sizeof(double), stream_);
+        if (e != cudaSuccess) return cuda_fail(e, "engine scalars");
+    }
+    Charge4 *keep_q = c->charges;
+    const int64_t keep_nc = c->Nc;
+    const cudaStream_t keep_stream = c->stream;
+    c->stream = stream_;
+    pb_status s = PB_OK;
+    for (int r = 0; r < mb->nrhs && s == PB_OK; ++r) {
+        c->charges = mb->q + r * mb->nc;
+        c->Nc = mb->nc;
+        s = energy_launch(c, mb->vec + (size_t)r * per + n2, PB_FP64, scalar_ + (r % 64));
+    }
+    c->charges = keep_q;
+    c->Nc = keep_nc;
+    c->stream = keep_stream;
+    if (s != PB_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(out, scalar_, mb->nrhs * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    return e == cudaSuccess ? PB_OK : cuda_fail(e, "engine energies");
+}
+
 }  // namespace pb
 
 // ---------------------------------------------------------------------------
-// Host side
+// pb_batch_solve: a fixed set of members solved to completion
 // ---------------------------------------------------------------------------
 using namespace pb;
-
-namespace {
-
-template <typename T>
-pb_status dalloc(pb_ctx *owner, T **p, size_t n, const char *what) {
-    return ctx_alloc(owner, (void **)p, n * sizeof(T), what);
-}
-
-}  // namespace
 
 extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double *const *charges, const int64_t *nc,
                                     const int *nrhs, const pb_solve_opts *opts, int use_graph, double *energies,
@@ -581,302 +894,59 @@ extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double
         return set_error(lead, PB_ERR_ARG, "pb_batch_solve: bad solve options");
     if (o.prec != PB_FP32PAIR)
         return set_error(lead, PB_ERR_ARG, "pb_batch_solve: the batched product is FP32-pair only");
-    int rmax = 0, nq = 0;
     for (int s = 0; s < nsurf; ++s) {
         if (!ctxs[s] || ctxs[s]->device != lead->device)
             return set_error(lead, PB_ERR_ARG, "pb_batch_solve: context %d is NULL or on another device", s);
-        if (nrhs[s] < 1 || nrhs[s] > kMaxRhs)
-            return set_error(lead, PB_ERR_ARG, "pb_batch_solve: nrhs[%d] = %d not in [1, %d]", s, nrhs[s], kMaxRhs);
+        if (nrhs[s] < 1 || nrhs[s] > kEngineMaxRhs)
+            return set_error(lead, PB_ERR_ARG, "pb_batch_solve: nrhs[%d] = %d not in [1, %d]", s, nrhs[s],
+                             kEngineMaxRhs);
         if (nc[s] < 0 || (nc[s] > 0 && !charges[s]))
             return set_error(lead, PB_ERR_ARG, "pb_batch_solve: bad charges for surface %d", s);
-        rmax = nrhs[s] > rmax ? nrhs[s] : rmax;
-        nq += nrhs[s];
     }
-    const int R = rmax <= 1 ? 1 : (rmax <= 2 ? 2 : (rmax <= 4 ? 4 : 8));
-    const cudaStream_t stream = lead->stream;
-    const int m = o.restart;
-
-    // host tables
-    std::vector<BSurf> hs(nsurf);
-    std::vector<BInst> hq(nq);
-    std::vector<BChunk> hch, hsch;
-    std::vector<Charge4> hcharges;
-    std::vector<double> h_inv_eps1(nsurf);
-    int64_t L = 0, tiles = 0, work = 0;
-    int qi = 0;
-    for (int s = 0; s < nsurf; ++s) {
-        pb_ctx *c = ctxs[s];
-        BSurf &sf = hs[s];
-        sf.pos = c->pos32;
-        sf.nrm = c->nrm32;
-        sf.g64 = c->g64;
-        sf.N = c->N;
-        sf.eps = (float)c->eps;
-        sf.inv_eps = (float)(1.0 / c->eps);
-        sf.kappa = (float)c->kappa;
-        sf.nk = (float)(-c->kappa * 1.4426950408889634);
-        sf.diag1 = 0.5 * (1.0 + c->eps);
-        sf.diag2 = 0.5 * (1.0 + 1.0 / c->eps);
-        const int64_t T = (c->N + kBThreads - 1) / kBThreads;
-        sf.S = (c->N + kBSourceTile - 1) / kBSourceTile;
-        sf.tile_base = tiles;
-        sf.work_base = work;
-        sf.inst0 = qi;
-        sf.nrhs = nrhs[s];
-        tiles += T;
-        work += T * sf.S;
-        h_inv_eps1[s] = 1.0 / c->eps1;
-        for (int r = 0; r < nrhs[s]; ++r, ++qi) {
-            BInst &in = hq[qi];
-            in.off = L;
-            in.n = c->N;
-            in.surf = s;
-            in.chunk0 = (int)hch.size();
-            for (int64_t st = 0; st < 2 * c->N; st += kChunk)
-                hch.push_back(BChunk{qi, (int)((2 * c->N - st) < kChunk ? (2 * c->N - st) : kChunk), L + st});
-            in.nchunk = (int)hch.size() - in.chunk0;
-            in.schunk0 = (int)hsch.size();
-            for (int64_t st = 0; st < c->N; st += kVThreads)
-                hsch.push_back(BChunk{qi, (int)((c->N - st) < kVThreads ? (c->N - st) : kVThreads), st});
-            in.nschunk = (int)hsch.size() - in.schunk0;
-            in.qoff = (int64_t)hcharges.size();
-            in.nc = nc[s];
-            const double *qs = charges[s] + (int64_t)r * nc[s] * 4;
-            for (int64_t k = 0; k < nc[s]; ++k)
-                hcharges.push_back(Charge4{qs[4 * k] - c->center[0], qs[4 * k + 1] - c->center[1],
-                                           qs[4 * k + 2] - c->center[2], qs[4 * k + 3]});
-            L += 2 * c->N;
-        }
-    }
-    const int nchunks = (int)hch.size(), nschunks = (int)hsch.size();
-    int occ = 0;
-    switch (R) {
-        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bmatvec_kernel<1>, kBThreads, 0); break;
-        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bmatvec_kernel<2>, kBThreads, 0); break;
-        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bmatvec_kernel<4>, kBThreads, 0); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bmatvec_kernel<8>, kBThreads, 0); break;
-    }
-    if (occ < 1) occ = 1;
-    int64_t G = (int64_t)lead->num_sms * occ;
-    if (G > work) G = work;
-
-    // device buffers (owned by the lead context's allocator, freed below)
-    BSurf *d_surf = nullptr;
-    BInst *d_inst = nullptr;
-    BChunk *d_ch = nullptr, *d_sch = nullptr;
-    Charge4 *d_q = nullptr;
-    double *d_ie = nullptr, *b = nullptr, *x = nullptr, *w = nullptr, *r = nullptr, *V = nullptr, *red = nullptr,
-           *part = nullptr, *en = nullptr;
-    GmresState *st = nullptr;
-    BStatus *d_status = nullptr, *h_status = nullptr;
-    unsigned int *cnt_inst = nullptr, *cnt_tile = nullptr;
-    unsigned long long *evals = nullptr;
-    int *act_step = nullptr, *act_ax = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    Engine eng(lead->stream, lead->device, lead->num_sms, o.restart, o.tol, o.maxit);
+    std::vector<EngineMember *> mem(nsurf, nullptr);
     pb_status s = PB_OK;
-    cudaError_t e = cudaSuccess;
-#define BA(ptr, n, what) \
-    if (s == PB_OK) s = dalloc(lead, &ptr, (size_t)(n), what)
-    BA(d_surf, nsurf, "batch surfaces");
-    BA(d_inst, nq, "batch instances");
-    BA(d_ch, nchunks, "batch chunks");
-    BA(d_sch, nschunks, "batch source chunks");
-    BA(d_q, hcharges.size() > 0 ? hcharges.size() : 1, "batch charges");
-    BA(d_ie, nsurf, "batch 1/eps1");
-    BA(b, L, "batch rhs");
-    BA(x, L, "batch x");
-    BA(w, L, "batch w");
-    BA(r, L, "batch r");
-    BA(V, (size_t)(m + 1) * L, "batch Krylov basis");
-    BA(red, (size_t)(m + 1) * (nchunks > nschunks ? nchunks : nschunks), "batch reductions");
-    BA(part, (size_t)2 * G * 2 * R * kBThreads, "batch partials");
-    BA(en, nq, "batch energies");
-    BA(st, nq, "batch states");
-    BA(d_status, nq, "batch status");
-    BA(cnt_inst, nq, "batch instance counters");
-    BA(cnt_tile, tiles, "batch tile counters");
-    BA(evals, nsurf, "batch product counters");
-    BA(act_step, nsurf, "batch flags");
-    BA(act_ax, nsurf, "batch flags");
-#undef BA
-    if (s == PB_OK) {
-        e = cudaMallocHost((void **)&h_status, nq * sizeof(BStatus));
-        if (e != cudaSuccess) s = cuda_error(lead, e, "batch pinned status");
+    for (int i = 0; i < nsurf && s == PB_OK; ++i) mem[i] = eng.add(ctxs[i], charges[i], nc[i], nrhs[i], (uint64_t)i, &s);
+    if (s != PB_OK) return set_error(lead, s, "%s", eng.error);
+    bool all = false;
+    for (int cyc = 0; cyc < o.maxit + 2 && s == PB_OK && !all; ++cyc) {
+        s = eng.cycle(use_graph != 0);
+        all = true;
+        for (EngineMember *mb : mem) all &= mb->finished;
     }
-    auto up = [&](void *dst, const void *src, size_t bytes) {
-        if (s == PB_OK && bytes) {
-            e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream);
-            if (e != cudaSuccess) s = cuda_error(lead, e, "batch upload");
-        }
-    };
-    up(d_surf, hs.data(), nsurf * sizeof(BSurf));
-    up(d_inst, hq.data(), nq * sizeof(BInst));
-    up(d_ch, hch.data(), nchunks * sizeof(BChunk));
-    up(d_sch, hsch.data(), nschunks * sizeof(BChunk));
-    up(d_q, hcharges.data(), hcharges.size() * sizeof(Charge4));
-    up(d_ie, h_inv_eps1.data(), nsurf * sizeof(double));
-    // the uploads read pageable host vectors: wait before they go out of scope
-    if (s == PB_OK && (e = cudaStreamSynchronize(stream)) != cudaSuccess) s = cuda_error(lead, e, "batch upload");
-    if (s == PB_OK) {
-        e = cudaMemsetAsync(cnt_inst, 0, nq * sizeof(unsigned int), stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(cnt_tile, 0, tiles * sizeof(unsigned int), stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, L * sizeof(double), stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(w, 0, L * sizeof(double), stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(evals, 0, nsurf * sizeof(unsigned long long), stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(act_ax, 0, nsurf * sizeof(int), stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(act_step, 0, nsurf * sizeof(int), stream);
-        if (e != cudaSuccess) s = cuda_error(lead, e, "batch init");
-    }
-    const int qb = (nq + 127) / 128, sb = (nsurf + 127) / 128;
-    int64_t matvec_launches = 0;
-    int cycle_kernels = 0;
-
-    auto launch_mv = [&](const double *uu, double *yy, const int *act) {
-        switch (R) {
-            case 1: bmatvec_kernel<1><<<(unsigned)G, kBThreads, 0, stream>>>(d_surf, nsurf, d_inst, work, G, uu, yy, act, part, cnt_tile, evals); break;
-            case 2: bmatvec_kernel<2><<<(unsigned)G, kBThreads, 0, stream>>>(d_surf, nsurf, d_inst, work, G, uu, yy, act, part, cnt_tile, evals); break;
-            case 4: bmatvec_kernel<4><<<(unsigned)G, kBThreads, 0, stream>>>(d_surf, nsurf, d_inst, work, G, uu, yy, act, part, cnt_tile, evals); break;
-            default: bmatvec_kernel<8><<<(unsigned)G, kBThreads, 0, stream>>>(d_surf, nsurf, d_inst, work, G, uu, yy, act, part, cnt_tile, evals); break;
-        }
-        ++cycle_kernels;
-        ++matvec_launches;
-    };
-    // one restart cycle of every instance
-    auto enqueue_cycle = [&]() {
-        launch_mv(x, w, act_ax);
-        bg_cycle_start<<<nchunks, kVThreads, 0, stream>>>(b, w, r, d_ch, d_inst, red, cnt_inst, st);
-        bg_scale<<<nchunks, kVThreads, 0, stream>>>(r, V, d_ch, st, 0);
-        bg_flags<<<sb, 128, 0, stream>>>(d_surf, nsurf, st, act_step, act_ax, 0);
-        cycle_kernels += 3;
-        for (int k = 0; k < m; ++k) {
-            double *vk = V + (int64_t)k * L;
-            launch_mv(vk, w, act_step);
-            bg_dots<<<dim3(nchunks, k + 1), kVThreads, 0, stream>>>(V, L, w, k, d_ch, d_inst, red, nchunks, cnt_inst, st);
-            bg_orth1<<<nchunks, kVThreads, 0, stream>>>(V, L, w, k, d_ch, d_inst, red, nchunks, cnt_inst, st);
-            bg_orth2<<<nchunks, kVThreads, 0, stream>>>(V, L, w, k, d_ch, d_inst, red, cnt_inst, st);
-            bg_scale<<<nchunks, kVThreads, 0, stream>>>(w, vk + L, d_ch, st, 1);
-            bg_flags<<<sb, 128, 0, stream>>>(d_surf, nsurf, st, act_step, act_ax, 0);
-            cycle_kernels += 5;
-        }
-        bg_trisolve<<<qb, 128, 0, stream>>>(st, nq);
-        bg_update_x<<<nchunks, kVThreads, 0, stream>>>(V, L, x, d_ch, st);
-        bg_flags<<<sb, 128, 0, stream>>>(d_surf, nsurf, st, act_step, act_ax, 1);
-        bg_status<<<qb, 128, 0, stream>>>(st, nq, d_status);
-        cycle_kernels += 4;
-    };
-
-    int cycles_run = 0;
-    if (s == PB_OK) {
-        bg_init<<<qb, 128, 0, stream>>>(st, nq, m, o.maxit, o.tol);
-        bg_source<<<nschunks, kVThreads, 0, stream>>>(d_sch, d_inst, d_surf, d_q, d_ie, b);
-        bg_norm<<<nchunks, kVThreads, 0, stream>>>(b, d_ch, d_inst, red, cnt_inst, st);
-        for (int q = 0; q < 3; ++q) PB_LAUNCHED();
-        e = cudaGetLastError();
-        if (e != cudaSuccess) s = cuda_error(lead, e, "batch setup kernels");
-    }
-    // a CUDA graph needs a capturable stream (not the legacy default stream)
-    if (s == PB_OK && use_graph && stream != nullptr) {
-        e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            enqueue_cycle();
-            cudaError_t e2 = cudaStreamEndCapture(stream, &graph);
-            if (e == cudaSuccess) e = e2;
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
-        if (e != cudaSuccess) s = cuda_error(lead, e, "batch graph capture");
-    }
-    const int kernels_per_cycle = cycle_kernels;
-    const int64_t mv_per_cycle = matvec_launches;
-    matvec_launches = 0;
-    const int max_cycles = o.maxit + 2;
-    for (int cyc = 0; s == PB_OK && cyc < max_cycles; ++cyc) {
-        if (gexec) {
-            e = cudaGraphLaunch(gexec, stream);
-            count_launches(kernels_per_cycle);
-            matvec_launches += mv_per_cycle;
-        } else {
-            cycle_kernels = 0;
-            enqueue_cycle();
-            count_launches(cycle_kernels);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h_status, d_status, nq * sizeof(BStatus), cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        if (e != cudaSuccess) {
-            s = cuda_error(lead, e, "batch cycle");
-            break;
-        }
-        ++cycles_run;
-        bool all = true;
-        for (int q = 0; q < nq; ++q) all &= (h_status[q].done != 0);
-        if (all) break;
-    }
-    // energies (Eq. (14)) of every instance, FP64 pairs, through the per-context
-    // kernel: point each context at the instance's charges and solution
-    int nconv = 0, iters_max = 0, iters_sum = 0;
+    if (s != PB_OK) return set_error(lead, s, "%s", eng.error);
+    int k = 0, nconv = 0, nq = 0, iters_max = 0;
+    int64_t iters_sum = 0;
     double resid_max = 0.0;
     pb_status worst = PB_OK;
-    if (s == PB_OK) {
-        for (int q = 0; q < nq && s == PB_OK; ++q) {
-            const BInst &in = hq[q];
-            pb_ctx *c = ctxs[in.surf];
-            // energy of instance q with its own charges: stage them in the context
-            Charge4 *keep = c->charges;
-            const int64_t keep_nc = c->Nc;
-            const cudaStream_t keep_stream = c->stream;
-            c->charges = d_q + in.qoff;
-            c->Nc = in.nc;
-            c->stream = stream;
-            s = energy_launch(c, x + in.off, PB_FP64, en + q);
-            c->charges = keep;
-            c->Nc = keep_nc;
-            c->stream = keep_stream;
+    for (int i = 0; i < nsurf && s == PB_OK; ++i) {
+        s = eng.energies(mem[i], energies + k);
+        for (int r = 0; r < nrhs[i]; ++r) {
+            const BStatus &b = mem[i]->status[r];
+            nconv += b.converged;
+            ++nq;
+            iters_max = b.iters > iters_max ? b.iters : iters_max;
+            iters_sum += b.iters;
+            resid_max = b.rel_resid > resid_max ? b.rel_resid : resid_max;
+            if (b.status == PB_ERR_NAN) worst = PB_ERR_NAN;
+            else if (!b.converged && worst == PB_OK) worst = PB_ERR_NOCONV;
         }
-        if (s == PB_OK) {
-            e = cudaMemcpyAsync(energies, en, nq * sizeof(double), cudaMemcpyDeviceToHost, stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-            if (e != cudaSuccess) s = cuda_error(lead, e, "batch energies");
-        }
-        for (int q = 0; q < nq; ++q) {
-            nconv += h_status[q].converged;
-            iters_max = h_status[q].iters > iters_max ? h_status[q].iters : iters_max;
-            iters_sum += h_status[q].iters;
-            resid_max = h_status[q].rel_resid > resid_max ? h_status[q].rel_resid : resid_max;
-            if (h_status[q].status == PB_ERR_NAN) worst = PB_ERR_NAN;
-            else if (!h_status[q].converged && worst == PB_OK) worst = PB_ERR_NOCONV;
-        }
+        k += nrhs[i];
     }
+    if (s != PB_OK) return set_error(lead, s, "%s", eng.error);
     if (info) {
         info->instances = nq;
         info->converged = nconv;
-        info->cycles = cycles_run;
+        info->cycles = eng.cycles_run;
         info->iters_max = iters_max;
         info->iters_sum = iters_sum;
         info->rel_resid_max = resid_max;
-        info->rhs_width = R;
-        info->ctas = G;
-        info->pair_evals = 0;
-        info->pair_products = 0;
-        info->matvec_launches = matvec_launches;
-        std::vector<unsigned long long> hev(nsurf, 0);
-        if (s == PB_OK && cudaMemcpy(hev.data(), evals, nsurf * sizeof(unsigned long long), cudaMemcpyDeviceToHost) ==
-                              cudaSuccess) {
-            for (int sidx = 0; sidx < nsurf; ++sidx) {
-                const int64_t pairs = hs[sidx].N * (hs[sidx].N - 1);
-                info->pair_evals += (int64_t)hev[sidx] * pairs;
-                info->pair_products += (int64_t)hev[sidx] * pairs * hs[sidx].nrhs;
-            }
-        }
+        info->rhs_width = eng.rhs_width;
+        info->ctas = eng.ctas;
+        info->pair_evals = eng.pair_evals;
+        info->pair_products = eng.pair_products;
+        info->matvec_launches = eng.matvec_launches;
     }
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (graph) cudaGraphDestroy(graph);
-    void *bufs[] = {d_surf, d_inst, d_ch, d_sch, d_q, d_ie, b, x, w, r, V, red, part, en, st, d_status,
-                    cnt_inst, cnt_tile, evals, act_step, act_ax};
-    for (void *p : bufs) ctx_free(lead, p);
-    cudaStreamSynchronize(stream);
-    if (h_status) cudaFreeHost(h_status);
-    if (s != PB_OK) return s;
     if (worst != PB_OK)
         return set_error(lead, worst, "pb_batch_solve: %d of %d instances did not converge", nq - nconv, nq);
     return PB_OK;
