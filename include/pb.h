@@ -188,6 +188,55 @@ pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double *const *ch
                          const int *nrhs, const pb_solve_opts *opts, int use_graph, double *energies,
                          pb_batch_info *info);
 
+/* Solve server with continuous batching (a library extension for serving;
+ * the paper runs one molecule per run).  pb_server_create starts a worker
+ * thread with its own CUDA stream on the current device.  pb_server_submit
+ * (any thread) copies a request (host arrays, same layout as pb_create) into
+ * the queue and returns its id.  The worker admits queued requests in arrival
+ * order while fewer than max_active are running and their estimated device
+ * footprint fits hbm_budget_bytes (larger than the whole budget: result
+ * status PB_ERR_ADMIT), and advances all running requests together one GMRES
+ * restart cycle at a time (FP32-pair products, FP64 Krylov arithmetic), so
+ * requests that arrive while others run join at the next cycle boundary.
+ * Results (energy of Eq. (14), status, latency from submit to result, time
+ * queued) are collected with pb_server_poll; pb_server_wait blocks until at
+ * least n results are waiting or the timeout passes (PB_ERR_TIMEOUT).
+ * pb_server_destroy drops requests not yet admitted, finishes the running
+ * ones, and frees everything. */
+typedef struct pb_server pb_server;
+typedef struct {
+    int max_active;           /* running requests at most (8 if <= 0) */
+    int64_t hbm_budget_bytes; /* device memory for running requests (8 GiB if <= 0) */
+    int restart;              /* GMRES restart (10 if <= 0) */
+    double tol;               /* relative residual (1e-4 if <= 0) */
+    int maxit;                /* Arnoldi steps per request (1000 if <= 0) */
+} pb_server_opts;
+typedef struct {
+    uint64_t id;
+    int status;               /* pb_status of the request */
+    int iters;
+    double energy_kcal;
+    double latency_ms;        /* submit -> result */
+    double queue_ms;          /* submit -> admission */
+    int64_t n;
+} pb_server_result;
+typedef struct {
+    int64_t submitted, admitted, rejected, completed, failed;
+    int64_t cycles;
+    int64_t pair_evals, pair_products;
+    int active, pending, max_active_seen;
+    int64_t used_bytes;
+} pb_server_stats;
+
+pb_status pb_server_create(const pb_server_opts *opts, pb_server **out);
+pb_status pb_server_submit(pb_server *sv, const double *centroids, const double *normals, const double *areas,
+                           int64_t N, const double *charges, int64_t Nc, double eps1, double eps2, double kappa,
+                           uint64_t *id);
+int pb_server_poll(pb_server *sv, pb_server_result *out, int max);
+pb_status pb_server_wait(pb_server *sv, int64_t n_results, double timeout_s);
+pb_status pb_server_get_stats(pb_server *sv, pb_server_stats *out);
+void pb_server_destroy(pb_server *sv);
+
 /* Kernel choice for the FP32-pair product (a tuning knob of this library; the
  * paper has a single FP64 kernel).  variant: 1 = scalar FP32, 4 targets per
  * thread; 2 = packed f32x2, 2 targets per thread; 3 = packed f32x2, 4 targets

@@ -44,6 +44,24 @@ class _BatchInfo(ctypes.Structure):
                 ("pair_products", ctypes.c_int64), ("matvec_launches", ctypes.c_int64)]
 
 
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64), ("restart", ctypes.c_int),
+                ("tol", ctypes.c_double), ("maxit", ctypes.c_int)]
+
+
+class _ServerResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("energy_kcal", ctypes.c_double), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("n", ctypes.c_int64)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("cycles", ctypes.c_int64),
+                ("pair_evals", ctypes.c_int64), ("pair_products", ctypes.c_int64), ("active", ctypes.c_int),
+                ("pending", ctypes.c_int), ("max_active_seen", ctypes.c_int), ("used_bytes", ctypes.c_int64)]
+
+
 class _CtxInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nc", ctypes.c_int64), ("eps1", ctypes.c_double),
                 ("eps2", ctypes.c_double), ("kappa", ctypes.c_double), ("center", ctypes.c_double * 3),
@@ -69,6 +87,12 @@ SIGNATURES = {
     "pb_profile_read": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), ctypes.POINTER(_I64), _I]),
     "pb_matvec_f32_static": (_I, [_VP, _VP, _VP, _I64, ctypes.POINTER(_D), _D, _D, _D, _VP, _VP, _VP]),
     "pb_matvec_configure": (_I, [_VP, _I, _I]),
+    "pb_server_create": (_I, [ctypes.POINTER(_ServerOpts), ctypes.POINTER(_VP)]),
+    "pb_server_submit": (_I, [_VP, _VP, _VP, _VP, _I64, _VP, _I64, _D, _D, _D, ctypes.POINTER(ctypes.c_uint64)]),
+    "pb_server_poll": (_I, [_VP, ctypes.POINTER(_ServerResult), _I]),
+    "pb_server_wait": (_I, [_VP, _I64, _D]),
+    "pb_server_get_stats": (_I, [_VP, ctypes.POINTER(_ServerStats)]),
+    "pb_server_destroy": (None, [_VP]),
     "pb_batch_solve": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I64), ctypes.POINTER(_I),
                             ctypes.POINTER(_Opts), _I, ctypes.POINTER(_D), ctypes.POINTER(_BatchInfo)]),
     "pb_matvec_get_config": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64)]),
@@ -338,6 +362,58 @@ def pb_batch_solve(ctxs, charge_sets, restart: int = 10, tol: float = 1e-4, maxi
     d = {f: getattr(info, f) for f, _ in _BatchInfo._fields_}
     d["status"] = st
     return out, d
+
+
+class Server:
+    """A solve server with continuous batching (pb_server_* of include/pb.h)."""
+
+    def __init__(self, max_active: int = 8, hbm_budget_bytes: int = 8 << 30, restart: int = 10,
+                 tol: float = 1e-4, maxit: int = 1000):
+        o = _ServerOpts(int(max_active), int(hbm_budget_bytes), int(restart), float(tol), int(maxit))
+        h = ctypes.c_void_p()
+        _check(lib().pb_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h.value
+
+    def submit(self, centroids, normals, areas, charges, eps1: float, eps2: float, kappa: float) -> int:
+        c = np.ascontiguousarray(centroids, dtype=np.float64)
+        nr = np.ascontiguousarray(normals, dtype=np.float64)
+        a = np.ascontiguousarray(areas, dtype=np.float64)
+        q = np.ascontiguousarray(charges, dtype=np.float64).reshape(-1, 4)
+        rid = ctypes.c_uint64()
+        _check(lib().pb_server_submit(self.handle, c.ctypes.data, nr.ctypes.data, a.ctypes.data, a.size,
+                                      q.ctypes.data if q.size else None, q.shape[0], float(eps1), float(eps2),
+                                      float(kappa), ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, max_results: int = 256) -> list:
+        buf = (_ServerResult * max_results)()
+        n = lib().pb_server_poll(self.handle, buf, max_results)
+        return [{f: getattr(buf[i], f) for f, _ in _ServerResult._fields_} for i in range(n)]
+
+    def wait(self, n_results: int, timeout_s: float) -> None:
+        _check(lib().pb_server_wait(self.handle, int(n_results), float(timeout_s)))
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(lib().pb_server_get_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in _ServerStats._fields_}
+
+    def close(self) -> None:
+        if self.handle:
+            h, self.handle = self.handle, None
+            lib().pb_server_destroy(h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pb_destroy(ctx: Context) -> None:
