@@ -36,19 +36,33 @@ METRIC = "matvec Gpairs/s; PB solves/s + p50/p99 latency at ≤1e-5 rel. energy 
 UNIT = "Gpairs/s"
 
 # Roofline of the FP32-pair matvec (ALU bound, no tensor-core contraction).
-# The algorithmic work per pair is 41 FP32 add/mul/fma operations plus 2 MUFU
-# operations (rsqrt, ex2).  The FP32 pipe retires 128 lanes per clock per SM,
-# MUFU 16, so the FP32 pipe binds: peak pairs/s = SMs x 128 x f_max / 41
-# (the MUFU ceiling, SMs x 16 x f_max / 2, is 2.6x higher).
-FP32_OPS_PER_PAIR = 41
+# The FP32 pipe retires 128 lanes per clock per SM (an f32x2 instruction
+# counts as two lanes' work), so for a kernel doing k FP32 add/mul/fma
+# operations per ordered pair, peak pairs/s = SMs x 128 x f_max / k.  MUFU
+# (16 per clock per SM, 2-3 per pair) and the ALU pipe are not binding.
+# k per variant (kappa > 0, kappa = 0), from the operation counts in the
+# kernels' comments; the symmetric kernels evaluate an unordered pair once for
+# both rows, so k is half their per-pair count.
 SMS = 152
 SM_MAX_MHZ = 2070.0
-PEAK_GPAIRS = SMS * 128 * SM_MAX_MHZ * 1e6 / FP32_OPS_PER_PAIR / 1e9
-# dram__bytes_read.sum + dram__bytes_write.sum of one matvec_f32_kernel launch
-# on the 81,920-triangle sphere, from the ncu capture summarised in
-# profiles/matvec_f32x2_kernel_sphere2_full.md; None once the kernel has changed.
-MATVEC_TRAFFIC_BYTES = {("matvec_f32_kernel", "sphere2"): 3988992}   # scalar kernel (variant 1)
-MATVEC_TRAFFIC_BYTES[("matvec_f32x2_kernel<4>", "sphere2")] = 3991296   # profiles/matvec_f32x2_kernel_sphere2_full.md
+MATVEC_KERNELS = {
+    1: ("matvec_f32_kernel", 41, 41),
+    2: ("matvec_f32x2_kernel<2>", 39, 18),
+    3: ("matvec_f32x2_kernel<4>", 39, 18),
+    4: ("matvec_f32x2_kernel<3>", 39, 18),
+    5: ("matvec_sym_kernel<2> + matvec_sym_finalize<2>", 23, 10),
+    6: ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", 23, 10),
+}
+
+
+def matvec_peak_gpairs(ops_per_pair):
+    return SMS * 128 * SM_MAX_MHZ * 1e6 / ops_per_pair / 1e9
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel on
+# the 81,920-triangle sphere, from an ncu capture of the kernel as it is now
+# (profiles/); a kernel that changed since its capture has no entry.
+MATVEC_TRAFFIC_BYTES = {}
 
 WORKLOADS = {
     "sphere2": "Kirkwood sphere R=20 A, icosphere level 6 (81,920 triangles), 20 charges in 0.8R, "
@@ -71,6 +85,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", choices=["solve", "batch", "serve"], default="solve",
+                    help="solve: one molecule per step (default); batch: 64 solutes x 8 charge sets per step; "
+                         "serve: Poisson request stream through the solve server")
+    ap.add_argument("--n-solutes", type=int, default=64, help="batch mode: solutes per batch")
+    ap.add_argument("--requests", type=int, default=48, help="serve mode: requests in the stream")
+    ap.add_argument("--pool", type=int, default=8, help="serve mode: distinct solutes the requests draw from")
+    ap.add_argument("--gen-workers", type=int, default=0, help="processes generating solute meshes (0: auto)")
     return ap.parse_args()
 
 
@@ -299,9 +320,11 @@ def run_ours(args):
     variant = variant_seen[-1]
 
     result = None
-    kname = "matvec_f64_kernel"
+    kname, ops = "matvec_f64_kernel", None
     if args.prec == "fp32pair":
-        kname = {1: "matvec_f32_kernel", 2: "matvec_f32x2_kernel<2>", 3: "matvec_f32x2_kernel<4>"}[variant]
+        kname, ops_k, ops_0 = MATVEC_KERNELS[variant]
+        ops = ops_0 if prob.kappa == 0.0 else ops_k
+    peak = matvec_peak_gpairs(ops) if ops else None
     if rank == 0:
         ref_e = golden_energy(args.workload)
         energies = [i.energy_kcal for i in infos]
@@ -317,11 +340,11 @@ def run_ours(args):
                 "gmres": {"iters": infos[-1].iters, "matvecs": infos[-1].matvecs,
                           "rel_resid": infos[-1].rel_resid},
                 "roofline": {"kernel": kname,
-                             "bound": "alu", "achieved": achieved, "peak": PEAK_GPAIRS, "unit": UNIT,
-                             "frac": achieved / PEAK_GPAIRS,
+                             "bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
+                             "frac": achieved / peak if peak else None,
                              "traffic": MATVEC_TRAFFIC_BYTES.get((kname, args.workload)),
                              "peak_basis": f"FP32 pipe: {SMS} SMs x 128 lanes x {SM_MAX_MHZ:.0f} MHz / "
-                                           f"{FP32_OPS_PER_PAIR} FP32 ops per pair (derived from unit counts "
+                                           f"{ops} FP32 ops per ordered pair (derived from unit counts "
                                            "and the maximum SM clock; not a measured peak)",
                              "avg_launch_ms": avg_ms, "launches": mv_n, "share_of_step": mv_share},
                 "gpu_launches": launches, "clocks": clocks}
@@ -361,10 +384,240 @@ def run_ours(args):
     return 0
 
 
+# --- batch and serve modes --------------------------------------------------------
+def _gen_solute(spec):
+    """Build one protein-like solute (top-level so a spawn pool can pickle it)."""
+    n_atoms, seed, target = spec
+    import pb_inputs
+    p = pb_inputs.protein_like(n_atoms=n_atoms, seed=seed, target_triangles=target)
+    s = p.surface
+    return s.centroids, s.normals, s.areas, p.charges
+
+
+def make_solutes(specs, workers):
+    """Generate meshes in a spawn process pool (started before any GPU call)."""
+    if workers <= 1:
+        return [_gen_solute(x) for x in specs]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_gen_solute, specs, chunksize=1)
+
+
+def batch_specs(n, seed=4):
+    """Atom counts floor(exp U[ln 50, ln 1500]); about 40 triangles per atom (N ~ 2k-60k)."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    atoms = np.floor(np.exp(rng.uniform(np.log(50), np.log(1500), size=n))).astype(int)
+    return [(int(a), 1000 + i, int(40 * a)) for i, a in enumerate(atoms)]
+
+
+def serve_specs(n, seed=5):
+    """N log-uniform in [5k, 300k]; atom count N/150 (the 2,000-atom solute gives ~300k)."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = np.exp(rng.uniform(np.log(5e3), np.log(3e5), size=n))
+    return [(max(20, int(x / 150)), 2000 + i, int(x)) for i, x in enumerate(ns)]
+
+
+def _workers(args):
+    return args.gen_workers if args.gen_workers > 0 else max(1, min(16, (os.cpu_count() or 2) - 1))
+
+
+def _clock_and_uuid(torch, dev):
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    return ClockSampler(uuid)
+
+
+BATCH_FP32_OPS_PER_EVAL = 37     # K1..K4 of one pair, scalar FP32 (2 MUFU besides)
+BATCH_FP32_OPS_PER_RHS = 4       # the two rows' accumulations per charge set
+
+
+def run_batch(args):
+    import numpy as np
+    import pb_inputs
+    specs = batch_specs(args.n_solutes)
+    sols = make_solutes(specs, _workers(args))
+    import torch
+    import paper_1301_5885_gb300 as pb
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    variants = [pb_inputs.charge_variants(q, 8, seed=3000 + i) for i, (_, _, _, q) in enumerate(sols)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        dev_in = [tuple(torch.tensor(a, device=dev) for a in (c, n, w, q)) for c, n, w, q in sols]
+        ctxs = [pb.pb_create(c, n, w, q, 1.0, 80.0, 0.1257, stream=stream) for c, n, w, q in dev_in]
+        ns = [c.n for c in ctxs]
+        for _ in range(args.warmup):
+            pb.pb_batch_solve(ctxs, variants, restart=args.restart, tol=args.tol, use_graph=True,
+                              raise_on_noconv=False)
+        stream.synchronize()
+        sampler = _clock_and_uuid(torch, dev)
+        sampler.start()
+        l0 = pb.pb_kernel_launches()
+        times, infos, energies = [], [], None
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            energies, info = pb.pb_batch_solve(ctxs, variants, restart=args.restart, tol=args.tol, use_graph=True,
+                                               raise_on_noconv=False)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(info)
+        launches = pb.pb_kernel_launches() - l0
+        clocks = sampler.stop()
+        # product kernel timing (one extra batch, kernels launched one by one with events)
+        _, tinfo = pb.pb_batch_solve(ctxs, variants, restart=args.restart, tol=args.tol, use_graph="timed",
+                                     raise_on_noconv=False)
+        # accuracy: the smallest surfaces, every charge set, against FP64 GPU solves at tol 1e-10
+        small = sorted(range(len(ctxs)), key=lambda i: ns[i])[:4]
+        errs = []
+        for i in small:
+            for r in range(8):
+                pb.pb_set_charges(ctxs[i], variants[i][r])
+                e64 = pb.pb_solve(ctxs[i], restart=10, tol=1e-10, maxit=3000, prec="fp64").energy_kcal
+                errs.append(abs(energies[i][r] - e64) / abs(e64))
+        for c in ctxs:
+            pb.pb_destroy(c)
+    total_ms = sum(times)
+    products = sum(i["pair_products"] for i in infos)
+    nsolve = sum(i["instances"] for i in infos)
+    width = tinfo["rhs_width"]
+    peak = SMS * 128 * SM_MAX_MHZ * 1e6 / ((BATCH_FP32_OPS_PER_EVAL + BATCH_FP32_OPS_PER_RHS * width) / width) / 1e9
+    achieved = tinfo["pair_products"] / (tinfo["matvec_ms"] * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": products / (total_ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs, f64 accumulation",
+            "data": "synthetic",
+            "config": {"workload": f"batch: {len(ctxs)} protein-like solutes (atoms log-uniform 50-1500, "
+                                   f"N {min(ns)}-{max(ns)}) x 8 charge variants, one lockstep batch per step",
+                       "n_triangles_total": int(sum(ns)), "instances": int(infos[-1]["instances"]),
+                       "gmres_restart": args.restart, "gmres_tol": args.tol, "cuda_graph": True,
+                       "l2": "flushed between steps (256 MiB write)"},
+            "solves_per_s": nsolve / (total_ms * 1e-3),
+            "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
+            "rel_energy_err": {"max_vs_fp64_gpu_smallest4x8": max(errs)},
+            "gmres": {"iters_max": infos[-1]["iters_max"], "cycles": infos[-1]["cycles"],
+                      "converged": f"{infos[-1]['converged']}/{infos[-1]['instances']}"},
+            "roofline": {"kernel": f"bmatvec_kernel<{width}>", "bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": UNIT, "frac": achieved / peak, "traffic": None,
+                         "peak_basis": f"FP32 pipe: {SMS} SMs x 128 lanes x {SM_MAX_MHZ:.0f} MHz / "
+                                       f"({BATCH_FP32_OPS_PER_EVAL} + {BATCH_FP32_OPS_PER_RHS} x {width}) / {width} "
+                                       "FP32 ops per pair and charge set (derived)",
+                         "products_ms": tinfo["matvec_ms"], "launches": tinfo["matvec_launches"]},
+            "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    import threading
+
+    import numpy as np
+    specs = serve_specs(args.pool)
+    pool = make_solutes(specs, _workers(args))
+    import torch
+    import paper_1301_5885_gb300 as pb
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    kappas = (0.0, 0.1257)
+    ns = [a.shape[0] for _, _, a, _ in pool]
+    budget = 96 << 30
+
+    def submit(sv, k, kap):
+        c, n, a, q = pool[k]
+        return sv.submit(c, n, a, q, 1.0, 80.0, kap)
+
+    # capacity: every pool solute at both kappas submitted at once
+    with pb.Server(max_active=16, hbm_budget_bytes=budget, tol=args.tol) as sv:
+        t = time.perf_counter()
+        for k in range(len(pool)):
+            for kap in kappas:
+                submit(sv, k, kap)
+        sv.wait(2 * len(pool), 3600.0)
+        cal = sv.poll(4096)
+        t_cal = time.perf_counter() - t
+    capacity = 2 * len(pool) / t_cal
+    rate = 0.7 * capacity
+    rng = np.random.Generator(np.random.PCG64(5))
+    gaps = rng.exponential(1.0 / rate, size=args.requests)
+    picks = rng.integers(0, len(pool), size=args.requests)
+    kaps = rng.integers(0, 2, size=args.requests)
+    sampler = _clock_and_uuid(torch, dev)
+    with pb.Server(max_active=16, hbm_budget_bytes=budget, tol=args.tol) as sv:
+        st0 = sv.stats()
+        sampler.start()
+        l0 = pb.pb_kernel_launches()
+        t_start = time.perf_counter()
+
+        def feeder():
+            for g, k, kk in zip(gaps, picks, kaps):
+                time.sleep(float(g))
+                submit(sv, int(k), kappas[int(kk)])
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        sv.wait(args.requests, 3600.0)
+        t_end = time.perf_counter()
+        res = sv.poll(4096)
+        st1 = sv.stats()
+        launches = pb.pb_kernel_launches() - l0
+        clocks = sampler.stop()
+    lat = np.array([r["latency_ms"] for r in res])
+    ok = all(r["status"] == pb.PB_OK for r in res)
+    wall = t_end - t_start
+    products = st1["pair_products"] - st0["pair_products"]
+    # one-at-a-time baselines on the same request mix, from per-item solve times
+    seq32, seq64, seq64_items = {}, {}, 0
+    with torch.cuda.stream(torch.cuda.Stream()):
+        for k in sorted(set(int(x) for x in picks)):
+            c, n, a, q = pool[k]
+            for kk in (0, 1):
+                with pb.pb_create(c, n, a, q, 1.0, 80.0, kappas[kk]) as ctx:
+                    t = time.perf_counter()
+                    pb.pb_solve(ctx, tol=args.tol, prec="fp32pair", raise_on_noconv=False)
+                    seq32[(k, kk)] = time.perf_counter() - t
+                    if ns[k] <= 20000:
+                        t = time.perf_counter()
+                        pb.pb_solve(ctx, tol=args.tol, prec="fp64", raise_on_noconv=False)
+                        seq64[(k, kk)] = time.perf_counter() - t
+    t32 = sum(seq32[(int(k), int(kk))] for k, kk in zip(picks, kaps))
+    sub = [(int(k), int(kk)) for k, kk in zip(picks, kaps) if (int(k), int(kk)) in seq64]
+    line = {"metric": METRIC, "value": products / wall / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.requests,
+            "warmup": 2 * len(pool), "ms_per_step": 1e3 * wall / args.requests, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs, f64 accumulation", "data": "synthetic",
+            "config": {"workload": f"serve: {args.requests} Poisson arrivals at 0.7 x measured capacity "
+                                   f"({rate:.2f}/s), drawn from {len(pool)} protein-like solutes with N "
+                                   f"log-uniform 5k-300k ({min(ns)}-{max(ns)}), kappa in {{0, 0.1257}}",
+                       "max_active": 16, "hbm_budget_bytes": budget, "gmres_tol": args.tol,
+                       "l2": "inputs exceed L2 across the stream; no flush"},
+            "solves_per_s": len(res) / wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean())},
+            "all_converged": ok, "max_active_seen": st1["max_active_seen"],
+            "baselines": {"sequential_fp32_solves_per_s": args.requests / t32,
+                          "sequential_fp64_solves_per_s_small_subset": (len(sub) / sum(seq64[x] for x in sub))
+                          if sub else None,
+                          "fp64_subset": f"{len(sub)} requests with N <= 20000"},
+            "capacity_solves_per_s": capacity, "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -164,9 +164,10 @@ pb_status pb_profile_read(pb_ctx *ctx, double *matvec_ms, int64_t *timed_launche
  * products; all instances advance in lockstep and each lockstep product is one
  * persistent launch over all surfaces that evaluates K1..K4 once per pair for
  * all charge sets of a surface.  All work runs on ctxs[0]'s stream; the other
- * contexts must not be in use meanwhile.  use_graph != 0 captures one restart
+ * contexts must not be in use meanwhile.  use_graph = 1 captures one restart
  * cycle of the whole batch in a CUDA graph and replays it (ignored on the
- * legacy default stream).  energies: host array of sum(nrhs) doubles (kcal/mol,
+ * legacy default stream); 0 launches the kernels one by one; 2 launches them
+ * one by one and times every product launch with CUDA events (matvec_ms).  energies: host array of sum(nrhs) doubles (kcal/mol,
  * Eq. (14)), in surface-major order.  Returns PB_ERR_NOCONV if an instance
  * reached maxit (energies still filled).  This is a library extension for
  * throughput; the paper solves one molecule per run. */
@@ -182,6 +183,8 @@ typedef struct {
     int64_t pair_evals;   /* K1..K4 pair evaluations, sum over products of N(N-1) */
     int64_t pair_products;/* pair evaluations times the charge sets they served */
     int64_t matvec_launches;
+    double matvec_ms;     /* summed CUDA-event time of the product launches
+                             (only measured when use_graph == 2) */
 } pb_batch_info;
 
 pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double *const *charges, const int64_t *nc,
@@ -240,7 +243,15 @@ void pb_server_destroy(pb_server *sv);
 /* Kernel choice for the FP32-pair product (a tuning knob of this library; the
  * paper has a single FP64 kernel).  variant: 1 = scalar FP32, 4 targets per
  * thread; 2 = packed f32x2, 2 targets per thread; 3 = packed f32x2, 4 targets
- * per thread; 0 = the stored or built-in default.  ctas_per_sm: resident CTAs
+ * per thread; 4 = packed f32x2, 3 targets per thread; 5 and 6 = symmetric
+ * packed f32x2 with 2 and 4 targets per thread (each unordered pair of
+ * Eqs. (12)-(13) evaluated once for both of its rows, using K1(i,j) = K1(j,i),
+ * K4(i,j) = K4(j,i) and the sign change of c_x, c_y under the exchange; two
+ * kernel launches per product; device scratch of about 4 N^2 / (128 t) bytes,
+ * t the targets per thread, allocated when the variant is configured and
+ * freed when another is; PB_ERR_OOM if it cannot be allocated); 0 = the
+ * stored or built-in default.  The packed variants use a kappa = 0
+ * specialisation when the context's kappa is 0.  ctas_per_sm: resident CTAs
  * per SM of the persistent grid, 0 = as many as fit.  Results differ between
  * variants only by FP32 rounding.  pb_matvec_autotune times every candidate
  * (reps launches each) on the context's geometry, keeps the fastest, and

@@ -41,7 +41,8 @@ class _BatchInfo(ctypes.Structure):
     _fields_ = [("instances", ctypes.c_int), ("converged", ctypes.c_int), ("cycles", ctypes.c_int),
                 ("iters_max", ctypes.c_int), ("iters_sum", ctypes.c_int64), ("rel_resid_max", ctypes.c_double),
                 ("rhs_width", ctypes.c_int), ("ctas", ctypes.c_int64), ("pair_evals", ctypes.c_int64),
-                ("pair_products", ctypes.c_int64), ("matvec_launches", ctypes.c_int64)]
+                ("pair_products", ctypes.c_int64), ("matvec_launches", ctypes.c_int64),
+                ("matvec_ms", ctypes.c_double)]
 
 
 class _ServerOpts(ctypes.Structure):
@@ -329,7 +330,7 @@ def pb_matvec_autotune(ctx: Context, reps: int = 3) -> dict:
 
 
 def pb_batch_solve(ctxs, charge_sets, restart: int = 10, tol: float = 1e-4, maxit: int = 1000,
-                   use_graph: bool = True, raise_on_noconv: bool = True):
+                   use_graph=True, raise_on_noconv: bool = True):
     """Solve every (surface, charge set) pair in lockstep.  ``ctxs``: list of
     contexts; ``charge_sets[s]``: array (R_s, Nc_s, 4) or (Nc_s, 4) of host
     charges.  Returns (energies as a list of R_s-length lists, info dict)."""
@@ -351,8 +352,8 @@ def pb_batch_solve(ctxs, charge_sets, restart: int = 10, tol: float = 1e-4, maxi
     en = (ctypes.c_double * total)()
     o = _Opts(int(restart), float(tol), int(maxit), PB_FP32PAIR, 0)
     info = _BatchInfo()
-    st = lib().pb_batch_solve(handles, n, ptrs, ncs, nr, ctypes.byref(o), 1 if use_graph else 0, en,
-                              ctypes.byref(info))
+    mode = 2 if use_graph == "timed" else (1 if use_graph else 0)
+    st = lib().pb_batch_solve(handles, n, ptrs, ncs, nr, ctypes.byref(o), mode, en, ctypes.byref(info))
     if st != PB_OK and not (st == PB_ERR_NOCONV and not raise_on_noconv):
         _check(st, ctxs[0])
     out, k = [], 0

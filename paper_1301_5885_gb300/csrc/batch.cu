@@ -502,6 +502,7 @@ Engine::~Engine() {
     if (graph_) cudaGraphDestroy(graph_);
     cudaStreamSynchronize(stream_);
     if (h_status_) cudaFreeHost(h_status_);
+    for (cudaEvent_t e : ev_) cudaEventDestroy(e);
 }
 
 pb_status Engine::fail(pb_status s, const char *fmt, ...) {
@@ -756,11 +757,16 @@ pb_status Engine::rebuild() {
 void Engine::enqueue_cycle() {
     const int sb = (nsurf_ + 127) / 128, qb = (nq_ + 127) / 128;
     auto mv = [&](int usel, int k, const int *act) {
+        if (timing_ && ev_used_ + 2 <= (int)ev_.size()) cudaEventRecord(ev_[ev_used_], stream_);
         switch (R_) {
             case 1: bmatvec_kernel<1><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
             case 2: bmatvec_kernel<2><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
             case 4: bmatvec_kernel<4><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
             default: bmatvec_kernel<8><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
+        }
+        if (timing_ && ev_used_ + 2 <= (int)ev_.size()) {
+            cudaEventRecord(ev_[ev_used_ + 1], stream_);
+            ev_used_ += 2;
         }
         ++cycle_kernels_;
         ++cycle_mv_;
@@ -785,11 +791,21 @@ void Engine::enqueue_cycle() {
     cycle_kernels_ += 3;
 }
 
-pb_status Engine::cycle(bool use_graph) {
+pb_status Engine::cycle(bool use_graph, bool time_products) {
     pb_status s = PB_OK;
     if (dirty_ && (s = rebuild()) != PB_OK) return s;
     if (nsurf_ == 0) return PB_OK;
     cudaError_t e = cudaSuccess;
+    if (time_products) {
+        use_graph = false;
+        if (ev_.empty()) {
+            ev_.resize(2 * (m_ + 2), nullptr);
+            for (auto &x : ev_)
+                if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(e, "engine events");
+        }
+        ev_used_ = 0;
+    }
+    timing_ = time_products;
     if (use_graph && stream_ != nullptr && !gexec_) {
         cycle_kernels_ = 0;
         cycle_mv_ = 0;
@@ -822,6 +838,11 @@ pb_status Engine::cycle(bool use_graph) {
         e = cudaMemcpyAsync(ev.data(), evals_, nsurf_ * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream_);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
     if (e != cudaSuccess) return cuda_fail(e, "engine cycle");
+    for (int i = 0; timing_ && i + 1 < ev_used_; i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev_[i], ev_[i + 1]) == cudaSuccess) matvec_ms += ms;
+    }
+    timing_ = false;
     ++cycles_run;
     int q = 0;
     for (int si = 0; si < nsurf_; ++si) {
@@ -910,7 +931,7 @@ extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double
     if (s != PB_OK) return set_error(lead, s, "%s", eng.error);
     bool all = false;
     for (int cyc = 0; cyc < o.maxit + 2 && s == PB_OK && !all; ++cyc) {
-        s = eng.cycle(use_graph != 0);
+        s = eng.cycle(use_graph == 1, use_graph == 2);
         all = true;
         for (EngineMember *mb : mem) all &= mb->finished;
     }
@@ -946,6 +967,7 @@ extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double
         info->pair_evals = eng.pair_evals;
         info->pair_products = eng.pair_products;
         info->matvec_launches = eng.matvec_launches;
+        info->matvec_ms = eng.matvec_ms;
     }
     if (worst != PB_OK)
         return set_error(lead, worst, "pb_batch_solve: %d of %d instances did not converge", nq - nconv, nq);

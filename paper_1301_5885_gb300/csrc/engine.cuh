@@ -49,8 +49,10 @@ class Engine {
     // Frees a member's device memory and drops it from the set.
     void remove(EngineMember *m);
     // One restart cycle of every unfinished instance (lockstep).  Fills the
-    // members' status and marks members whose instances are all done.
-    pb_status cycle(bool use_graph);
+    // members' status and marks members whose instances are all done.  With
+    // time_products (no graph), the product launches are bracketed by CUDA
+    // events and their time is added to matvec_ms.
+    pb_status cycle(bool use_graph, bool time_products = false);
     // Eq. (14) for every instance of a member (FP64 pairs), kcal/mol.
     pb_status energies(EngineMember *m, double *out);
     // Bytes one member of N triangles with nrhs sets needs (vectors and states).
@@ -58,6 +60,7 @@ class Engine {
 
     const std::vector<EngineMember *> &members() const { return members_; }
     int64_t matvec_launches = 0;
+    double matvec_ms = 0.0;      // event time of timed product launches
     int64_t pair_evals = 0;      // K1..K4 pair evaluations of the products
     int64_t pair_products = 0;   // times the charge sets they served
     int cycles_run = 0;
@@ -95,6 +98,9 @@ class Engine {
     cudaGraphExec_t gexec_ = nullptr;
     cudaGraph_t graph_ = nullptr;
     int kernels_per_cycle_ = 0, mv_per_cycle_ = 0, cycle_kernels_ = 0, cycle_mv_ = 0;
+    bool timing_ = false;
+    std::vector<cudaEvent_t> ev_;
+    int ev_used_ = 0;
 };
 
 }  // namespace pb

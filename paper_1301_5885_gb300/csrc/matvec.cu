@@ -44,6 +44,24 @@ StreamKPlan make_plan(int64_t n, int target_tile, int source_tile, int64_t ctas_
     return p;
 }
 
+SymPlan make_sym_plan(int64_t n, int tile, int64_t ctas_wanted) {
+    SymPlan p;
+    p.tiles = (n + tile - 1) / tile;
+    p.work = p.tiles * (p.tiles + 1) / 2;
+    p.ctas = ctas_wanted < 1 ? 1 : (ctas_wanted > p.work ? p.work : ctas_wanted);
+    return p;
+}
+
+namespace {
+int64_t round256(int64_t b) { return (b + 255) / 256 * 256; }
+}  // namespace
+
+int64_t sym_scratch_bytes(const SymPlan &pl, int tile) {
+    return round256(pl.tiles * 2 * tile * (int64_t)sizeof(double)) +
+           round256(pl.ctas * 2 * 2 * tile * (int64_t)sizeof(double)) +
+           round256((pl.work - pl.tiles) * 2 * tile * (int64_t)sizeof(float));
+}
+
 namespace {
 
 struct F32Params {
@@ -209,9 +227,20 @@ matvec_f32_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
 //   {-x0, -x1, -y0, -y1}  {-z0, -z1, nx0, nx1}  {ny0, ny1, nz0, nz1}  {Wdphi0, Wdphi1, Wphi0, Wphi1}
 // (W carries the 1/(4 pi)).  Each thread owns T targets, duplicated into both
 // halves of register pairs.  The singular self pair (and any pair at zero
-// distance) is removed by clamping 1/rho at 1e12: then rho = r2 * (1/rho) is
-// exactly 0, exp2(0) is exactly 1, c_x = c_y = 0, and every term of K1..K4 is an
-// exact zero, with no infinity formed.  Real pairs have 1/rho < 1e12 (rho > 1e-12 A).
+// distance) is removed by clamping 1/rho at 1e9 and 1/rho^2 at 1e18: then
+// rho = r2 * (1/rho) is exactly 0, exp2(0) is exactly 1, c_x = c_y = 0, and
+// every term of K1..K4 is an exact zero.  The weights times 1/rho^3 <= 1e27
+// stay finite for |W u| < 3e11, so no infinity is formed.  Real pairs have
+// 1/rho < 1e9 (rho > 1e-9 A).
+//
+// Per pair and kappa > 0 the FP32 pipe does 39 operations: r (3), rho^2 (3),
+// rho (1), the exp2 argument (1), kappa rho (1), e (1 + kappa rho) (1),
+// 1/rho^3 (1), c_x c_y n (9), the weights folded with 1/rho and 1/rho^3 (3),
+// K1 (2), K2 (3), K3 (3), K4 (5), 3 + 3 kappa rho + (kappa rho)^2 and e times
+// it (3); 1/rho^2 comes from the MUFU reciprocal.  With kappa = 0, e = 1 makes
+// K1 = K4 = 0 and K2, K3 reduce to (eps - 1) c_y / rho^3 and (1/eps - 1)
+// c_x / rho^3 (the constants folded into the staged weights): 18 operations
+// (r 3, rho^2 3, 1/rho^2 and 1/rho^3 2, c_x c_y 6, weights 2, sums 2).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -219,9 +248,16 @@ __device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(
 __device__ __forceinline__ float2 p_dup(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
 
-constexpr float kInvRhoMax = 1e12f;
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
-template <int T>
+constexpr float kInvRhoMax = 1e9f;
+constexpr float kInvRho2Max = 1e18f;
+
+template <int T, bool K0>
 __global__ void __launch_bounds__(kF32Threads)
 matvec_f32x2_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm,
                     const double *__restrict__ u, int64_t N, F32Params prm, StreamKPlan plan,
@@ -241,6 +277,8 @@ matvec_f32x2_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ n
     const float2 eps2 = p_dup(prm.eps), ieps2 = p_dup(prm.inv_eps), kap2 = p_dup(prm.kappa);
     const float2 nk2 = p_dup(prm.neg_kappa_log2e);
     const float2 one2 = p_dup(1.f), mone2 = p_dup(-1.f), three2 = p_dup(3.f), mthree2 = p_dup(-3.f);
+    // kappa = 0: the constant factors of K2 and K3, folded into the weights
+    const float wphi_scale = K0 ? prm.eps - 1.f : 1.f, wpsi_scale = K0 ? prm.inv_eps - 1.f : 1.f;
 
     while (p < pend) {
         const int64_t a = p / S;
@@ -273,8 +311,8 @@ matvec_f32x2_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ n
                     s_a[tid] = make_float4(-p0.x, -p1.x, -p0.y, -p1.y);
                     s_b[tid] = make_float4(-p0.z, -p1.z, n0.x, n1.x);
                     s_c[tid] = make_float4(n0.y, n1.y, n0.z, n1.z);
-                    s_d[tid] = make_float4((float)u[N + j0] * w0, (float)u[N + j1] * w1, (float)u[j0] * w0,
-                                           (float)u[j1] * w1);
+                    s_d[tid] = make_float4((float)u[N + j0] * (w0 * wpsi_scale), (float)u[N + j1] * (w1 * wpsi_scale),
+                                           (float)u[j0] * (w0 * wphi_scale), (float)u[j1] * (w1 * wphi_scale));
                 }
             }
             __syncthreads();
@@ -293,30 +331,41 @@ matvec_f32x2_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ n
                 for (int t = 0; t < T; ++t) {
                     const float2 dx = p_add(xi[t], mx), dy = p_add(yi[t], my), dz = p_add(zi[t], mz);
                     const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
-                    float2 inv;
+                    float2 inv, inv2;
                     inv.x = fminf(rsqrt_approx(r2.x), kInvRhoMax);
                     inv.y = fminf(rsqrt_approx(r2.y), kInvRhoMax);
-                    const float2 rho = p_mul(r2, inv);
-                    const float2 arg = p_mul(nk2, rho);
-                    float2 e;
-                    e.x = exp2_approx(arg.x);
-                    e.y = exp2_approx(arg.y);
-                    const float2 kr = p_mul(kap2, rho);
-                    const float2 e1 = p_fma(e, kr, e);                    // e (1 + kappa rho)
-                    const float2 inv2 = p_mul(inv, inv);
+                    if (K0) {
+                        inv2 = p_mul(inv, inv);                // MUFU is busier than the FP32 pipe here
+                    } else {
+                        inv2.x = fminf(rcp_approx(r2.x), kInvRho2Max);
+                        inv2.y = fminf(rcp_approx(r2.y), kInvRho2Max);
+                    }
                     const float2 inv3 = p_mul(inv2, inv);
                     const float2 cx = p_fma(dx, nxi[t], p_fma(dy, nyi[t], p_mul(dz, nzi[t])));
                     const float2 cy = p_fma(dx, snx, p_fma(dy, sny, p_mul(dz, snz)));
-                    const float2 nn = p_fma(nxi[t], snx, p_fma(nyi[t], sny, p_mul(nzi[t], snz)));
-                    const float2 k1 = p_mul(p_fma(e, mone2, one2), inv);   // (1 - e)/rho
-                    const float2 k2 = p_mul(p_mul(p_fma(eps2, e1, mone2), cy), inv3);
-                    const float2 k3 = p_mul(p_mul(p_fma(e1, ieps2, mone2), cx), inv3);
-                    const float2 p3 = p_fma(kr, p_add(kr, three2), three2);   // 3 + 3 kr + kr^2
-                    const float2 e3 = p_fma(e, p3, mthree2);
-                    const float2 ccy = p_mul(p_mul(e3, cx), cy);
-                    const float2 k4 = p_mul(p_fma(p_neg(ccy), inv2, p_fma(e1, nn, p_neg(nn))), inv3);
-                    f1[t] = p_fma(k1, wpsi, p_fma(k2, wphi, f1[t]));
-                    f2[t] = p_fma(k3, wpsi, p_fma(k4, wphi, f2[t]));
+                    const float2 wa = p_mul(inv3, wphi);       // W phi / rho^3
+                    const float2 wb = p_mul(inv3, wpsi);       // W dphi / rho^3
+                    if (K0) {
+                        f1[t] = p_fma(cy, wa, f1[t]);          // (eps - 1) c_y / rho^3, constant in wphi
+                        f2[t] = p_fma(cx, wb, f2[t]);          // (1/eps - 1) c_x / rho^3, constant in wpsi
+                    } else {
+                        const float2 rho = p_mul(r2, inv);
+                        const float2 arg = p_mul(nk2, rho);
+                        float2 e;
+                        e.x = exp2_approx(arg.x);
+                        e.y = exp2_approx(arg.y);
+                        const float2 kr = p_mul(kap2, rho);
+                        const float2 e1 = p_fma(e, kr, e);                    // e (1 + kappa rho)
+                        const float2 nn = p_fma(nxi[t], snx, p_fma(nyi[t], sny, p_mul(nzi[t], snz)));
+                        const float2 wc = p_mul(inv, wpsi);                   // W dphi / rho
+                        f1[t] = p_fma(p_fma(e, mone2, one2), wc, f1[t]);     // K1
+                        f1[t] = p_fma(p_mul(p_fma(eps2, e1, mone2), cy), wa, f1[t]);     // K2
+                        f2[t] = p_fma(p_mul(p_fma(e1, ieps2, mone2), cx), wb, f2[t]);    // K3
+                        const float2 p3 = p_fma(kr, p_add(kr, three2), three2);   // 3 + 3 kr + kr^2
+                        const float2 e3 = p_fma(e, p3, mthree2);
+                        const float2 ccy = p_mul(p_mul(e3, cx), cy);
+                        f2[t] = p_fma(p_fma(p_neg(ccy), inv2, p_fma(e1, nn, p_neg(nn))), wa, f2[t]);   // K4
+                    }
                 }
             }
 #pragma unroll
@@ -327,6 +376,317 @@ matvec_f32x2_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ n
         }
         finish_segment<TT, T, BS>(plan, a, c, acc1, acc2, u, N, prm.diag1, prm.diag2, partials, counters, y);
         p += s_end - s_first;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric evaluation.  K1 and K4 do not change when the two points (with
+// their normals) are exchanged, and the K2 / K3 of the reversed pair are the
+// same scalars times -c_x and -c_y.  With r = x_i - x_j,
+//   row i (source j): K1 dphi_j + a c_y phi_j,   b c_x dphi_j + K4 phi_j
+//   row j (source i): K1 dphi_i - a c_x phi_i,  -b c_y dphi_i + K4 phi_i
+// where a = (eps e (1 + kappa rho) - 1)/rho^3, b = (e (1 + kappa rho)/eps - 1)/rho^3,
+// so one evaluation of the unordered pair serves both rows.
+//
+// The targets are cut into square tiles of B = 128 T points and the upper
+// triangle of tile pairs (I <= J) is split evenly over persistent CTAs.  A
+// diagonal pair (I, I) is evaluated plainly (every ordered pair, row side
+// only).  For I < J the row-i side accumulates in registers across the J of
+// a CTA's run, as in the plain kernel; the row-j ("column") side is summed
+// over the thread's targets, then over the warp with a reduce-scatter (6
+// shuffles per source pair), then over the 4 warps in shared memory, and
+// stored per tile pair in FP32.  A second kernel adds, for every row, its row
+// side and the column sides of all tile pairs above it in a fixed order:
+// deterministic, no floating-point atomics.
+//
+// Signs are arranged so that no operand needs negating: the target normals
+// are negated when loaded (c_x and n change sign), 1 - e (1 + kappa rho) is
+// formed instead of e (1 + kappa rho) - 1, and b enters negated.  Per
+// unordered pair and kappa > 0 the FP32 pipe does 46 operations (r 3,
+// rho^2 3, 1/rho^3 1, c_x c_y n 9, rho, the exp2 argument and -kappa rho 3,
+// 1 - e and 1 - e (1 + kappa rho) 2, K1 1, a 2, -b 2, K4 8, row side 6,
+// column side 6): 23 per ordered pair against 39.  With kappa = 0 it is 20
+// (r 3, rho^2 3, 1/rho^2 and 1/rho^3 2, c_x c_y 6, c/rho^3 2, four sums),
+// the constants (eps - 1) and (1 - 1/eps) folded into the weights.
+// ---------------------------------------------------------------------------
+// first tile pair of row tile I (pairs are numbered row by row)
+__host__ __device__ inline int64_t sym_row_start(int64_t I, int64_t tiles) { return I * tiles - I * (I - 1) / 2; }
+// row tile of tile pair p
+__host__ __device__ inline int64_t sym_row_of(int64_t p, int64_t tiles) {
+    int64_t lo = 0, hi = tiles - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (sym_row_start(mid, tiles) <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+// slot of off-diagonal tile pair (I, J), J > I, among the off-diagonal pairs
+__host__ __device__ inline int64_t sym_offdiag_index(int64_t I, int64_t J, int64_t tiles) {
+    return sym_row_start(I, tiles) + (J - I) - I - 1;
+}
+
+// Sums four values g1 = (A, B), g2 = (C, D) over the warp: lanes 0-7 end with
+// the total of A, 8-15 of B, 16-23 of C, 24-31 of D.
+__device__ __forceinline__ float reduce_scatter4(float2 g1, float2 g2) {
+    const int lane = threadIdx.x & 31;
+    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+    float2 keep = hi16 ? g2 : g1;
+    const float2 send = hi16 ? g1 : g2;
+    keep.x += __shfl_xor_sync(0xffffffffu, send.x, 16);
+    keep.y += __shfl_xor_sync(0xffffffffu, send.y, 16);
+    float k = hi8 ? keep.y : keep.x;
+    const float o = hi8 ? keep.x : keep.y;
+    k += __shfl_xor_sync(0xffffffffu, o, 8);
+    k += __shfl_xor_sync(0xffffffffu, k, 4);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    return k;
+}
+
+struct SymConsts {
+    float2 nk2, mkap2, one2, mone2, mthree2, three2, meps2, epsm1, ieps2, omieps;
+};
+
+// One staged source tile against the thread's T targets: the row sides into
+// f1, f2 and, with COL, the column sides of each source pair reduced over the
+// warp into col (lanes 0-7: f1 side of the pair's first source, 8-15 of its
+// second, 16-23 and 24-31: f2 side; col[k] and col[B + k] for source k of the
+// tile).  The reduction of pair q is issued after the arithmetic of pair
+// q + 1 so that its shuffle chain overlaps that work.
+template <int T, bool K0, bool COL>
+__device__ __forceinline__ void sym_stage(const float4 *s_a, const float4 *s_b, const float4 *s_c,
+                                          const float4 *s_d, int npairs, const float2 (&xi)[T],
+                                          const float2 (&yi)[T], const float2 (&zi)[T], const float2 (&nxi)[T],
+                                          const float2 (&nyi)[T], const float2 (&nzi)[T], const float2 (&wpi)[T],
+                                          const float2 (&wfi)[T], float2 (&f1)[T], float2 (&f2)[T], float *col,
+                                          const SymConsts &k) {
+    constexpr int B = kF32Threads * T;
+    const int lane = threadIdx.x & 31;
+    float2 pg1 = p_dup(0.f), pg2 = p_dup(0.f);
+    for (int q = 0; q < npairs; ++q) {
+        const float4 A = s_a[q], Bq = s_b[q], C = s_c[q], D = s_d[q];
+        const float2 mx = make_float2(A.x, A.y), my = make_float2(A.z, A.w), mz = make_float2(Bq.x, Bq.y);
+        const float2 snx = make_float2(Bq.z, Bq.w), sny = make_float2(C.x, C.y), snz = make_float2(C.z, C.w);
+        const float2 wpsi = make_float2(D.x, D.y), wphi = make_float2(D.z, D.w);
+        float2 g1 = p_dup(0.f), g2 = p_dup(0.f);     // column sides of the two sources
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const float2 dx = p_add(xi[t], mx), dy = p_add(yi[t], my), dz = p_add(zi[t], mz);
+            const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
+            float2 inv, inv2;
+            inv.x = fminf(rsqrt_approx(r2.x), kInvRhoMax);
+            inv.y = fminf(rsqrt_approx(r2.y), kInvRhoMax);
+            if (K0) {
+                inv2 = p_mul(inv, inv);
+            } else {
+                inv2.x = fminf(rcp_approx(r2.x), kInvRho2Max);
+                inv2.y = fminf(rcp_approx(r2.y), kInvRho2Max);
+            }
+            const float2 inv3 = p_mul(inv2, inv);
+            const float2 ncx = p_fma(dx, nxi[t], p_fma(dy, nyi[t], p_mul(dz, nzi[t])));   // -c_x
+            const float2 cy = p_fma(dx, snx, p_fma(dy, sny, p_mul(dz, snz)));
+            if (K0) {
+                const float2 ay = p_mul(cy, inv3), bx = p_mul(ncx, inv3);
+                f1[t] = p_fma(ay, wphi, f1[t]);
+                f2[t] = p_fma(bx, wpsi, f2[t]);
+                if (COL) {
+                    g1 = p_fma(bx, wfi[t], g1);
+                    g2 = p_fma(ay, wpi[t], g2);
+                }
+            } else {
+                const float2 rho = p_mul(r2, inv);
+                float2 e;
+                const float2 arg = p_mul(k.nk2, rho);
+                e.x = exp2_approx(arg.x);
+                e.y = exp2_approx(arg.y);
+                const float2 mkr = p_mul(k.mkap2, rho);                             // -kappa rho
+                const float2 nnn = p_fma(nxi[t], snx, p_fma(nyi[t], sny, p_mul(nzi[t], snz)));   // -n
+                const float2 ome = p_fma(e, k.mone2, k.one2);                       // 1 - e
+                const float2 ome1 = p_fma(e, mkr, ome);                             // 1 - e (1 + kappa rho)
+                const float2 k1 = p_mul(ome, inv);
+                const float2 al = p_mul(p_fma(ome1, k.meps2, k.epsm1), inv3);       // a
+                const float2 nb = p_mul(p_fma(ome1, k.ieps2, k.omieps), inv3);      // -b
+                const float2 p3 = p_fma(mkr, p_add(mkr, k.mthree2), k.three2);      // 3 + 3 kappa rho + (kappa rho)^2
+                const float2 e3 = p_fma(e, p3, k.mthree2);
+                const float2 ccy = p_mul(p_mul(e3, ncx), cy);                       // -e3 c_x c_y
+                const float2 k4 = p_mul(p_fma(ccy, inv2, p_mul(ome1, nnn)), inv3);
+                f1[t] = p_fma(k1, wpsi, p_fma(p_mul(al, cy), wphi, f1[t]));
+                f2[t] = p_fma(p_mul(nb, ncx), wpsi, p_fma(k4, wphi, f2[t]));
+                if (COL) {
+                    g1 = p_fma(k1, wpi[t], p_fma(p_mul(al, ncx), wfi[t], g1));
+                    g2 = p_fma(p_mul(nb, cy), wpi[t], p_fma(k4, wfi[t], g2));
+                }
+            }
+        }
+        if (COL) {
+            if (q > 0) {
+                const float tot = reduce_scatter4(pg1, pg2);
+                if ((lane & 7) == 0) col[(lane >> 4) * B + 2 * (q - 1) + ((lane >> 3) & 1)] = tot;
+            }
+            pg1 = g1;
+            pg2 = g2;
+        }
+    }
+    if (COL && npairs > 0) {
+        const float tot = reduce_scatter4(pg1, pg2);
+        if ((lane & 7) == 0) col[(lane >> 4) * B + 2 * (npairs - 1) + ((lane >> 3) & 1)] = tot;
+    }
+}
+
+template <int T, bool K0>
+__global__ void __launch_bounds__(kF32Threads, T >= 4 ? 3 : 4)
+matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm, const double *__restrict__ u,
+                  int64_t N, F32Params prm, SymPlan plan, double *__restrict__ islots, double *__restrict__ iside,
+                  float *__restrict__ jpart, const int *__restrict__ skip, unsigned long long *__restrict__ evaluated) {
+    constexpr int BS = kF32Threads, B = BS * T, TS = kF32SourceTile, TQ = TS / 2, NW = BS / 32;
+    constexpr int STAGES = B / TS;
+    static_assert(TQ == BS && B % TS == 0, "tile shapes");
+    if (skip != nullptr && *((volatile const int *)skip)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
+    __shared__ float4 s_a[TQ], s_b[TQ], s_c[TQ], s_d[TQ];
+    __shared__ float s_col[NW][2][B];     // per-warp column sides of the current tile pair
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t c = blockIdx.x;
+    const int64_t Tt = plan.tiles;
+    int64_t p = sk_begin(c, plan.work, plan.ctas);
+    const int64_t pend = sk_begin(c + 1, plan.work, plan.ctas);
+    const int64_t I_first = sym_row_of(p, Tt);
+    SymConsts c3;
+    c3.nk2 = p_dup(prm.neg_kappa_log2e);
+    c3.mkap2 = p_dup(-prm.kappa);
+    c3.one2 = p_dup(1.f);
+    c3.mone2 = p_dup(-1.f);
+    c3.mthree2 = p_dup(-3.f);
+    c3.three2 = p_dup(3.f);
+    c3.meps2 = p_dup(-prm.eps);
+    c3.epsm1 = p_dup(prm.eps - 1.f);
+    c3.ieps2 = p_dup(prm.inv_eps);
+    c3.omieps = p_dup(1.f - prm.inv_eps);
+    // kappa = 0: a = (eps - 1)/rho^3 and -b = (1 - 1/eps)/rho^3, constants folded into the weights
+    const float wphi_scale = K0 ? prm.eps - 1.f : 1.f, wpsi_scale = K0 ? 1.f - prm.inv_eps : 1.f;
+
+    while (p < pend) {
+        const int64_t I = sym_row_of(p, Tt);
+        const int64_t row_end = sym_row_start(I + 1, Tt);
+        const int64_t p_stop = pend < row_end ? pend : row_end;
+        // row tile targets: position, negated normal, weights of their own u (column side)
+        float2 xi[T], yi[T], zi[T], nxi[T], nyi[T], nzi[T], wpi[T], wfi[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int64_t i0 = I * B + t * BS + tid;
+            const int64_t i = i0 < N ? i0 : N - 1;
+            const float4 q = pos[i], n = nrm[i];
+            xi[t] = p_dup(q.x); yi[t] = p_dup(q.y); zi[t] = p_dup(q.z);
+            nxi[t] = p_dup(-n.x); nyi[t] = p_dup(-n.y); nzi[t] = p_dup(-n.z);
+            const float w = i0 < N ? q.w : 0.f;
+            wpi[t] = p_dup((float)u[N + i] * (w * wpsi_scale));
+            wfi[t] = p_dup((float)u[i] * (w * wphi_scale));
+        }
+        double acc1[T], acc2[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) { acc1[t] = 0.0; acc2[t] = 0.0; }
+
+        for (; p < p_stop; ++p) {
+            const int64_t J = I + (p - sym_row_start(I, Tt));
+            const bool diag = (J == I);
+            for (int stg = 0; stg < STAGES; ++stg) {
+                const int64_t s0 = J * B + stg * TS;
+                if (s0 >= N) break;
+                __syncthreads();
+                {
+                    const int64_t j0 = s0 + 2 * tid;
+                    if (j0 < N) {
+                        const int64_t j1 = (j0 + 1 < N) ? j0 + 1 : j0;
+                        const float4 p0 = pos[j0], p1 = pos[j1], n0 = nrm[j0], n1 = nrm[j1];
+                        const float w0 = p0.w, w1 = (j0 + 1 < N) ? p1.w : 0.f;
+                        s_a[tid] = make_float4(-p0.x, -p1.x, -p0.y, -p1.y);
+                        s_b[tid] = make_float4(-p0.z, -p1.z, n0.x, n1.x);
+                        s_c[tid] = make_float4(n0.y, n1.y, n0.z, n1.z);
+                        s_d[tid] = make_float4((float)u[N + j0] * (w0 * wpsi_scale),
+                                               (float)u[N + j1] * (w1 * wpsi_scale),
+                                               (float)u[j0] * (w0 * wphi_scale), (float)u[j1] * (w1 * wphi_scale));
+                    }
+                }
+                __syncthreads();
+                const int64_t rem = N - s0;
+                const int npairs = (int)(((rem < TS) ? rem : TS) + 1) / 2;
+                float2 f1[T], f2[T];
+#pragma unroll
+                for (int t = 0; t < T; ++t) { f1[t] = p_dup(0.f); f2[t] = p_dup(0.f); }
+                if (diag)
+                    sym_stage<T, K0, false>(s_a, s_b, s_c, s_d, npairs, xi, yi, zi, nxi, nyi, nzi, wpi, wfi, f1, f2,
+                                            nullptr, c3);
+                else
+                    sym_stage<T, K0, true>(s_a, s_b, s_c, s_d, npairs, xi, yi, zi, nxi, nyi, nzi, wpi, wfi, f1, f2,
+                                           &s_col[warp][0][stg * TS], c3);
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    acc1[t] += (double)f1[t].x + (double)f1[t].y;
+                    acc2[t] += (double)f2[t].x + (double)f2[t].y;
+                }
+            }
+            if (!diag) {
+                // column side of tile pair (I, J): sum over the warps in a fixed order
+                __syncthreads();
+                float *dst = jpart + sym_offdiag_index(I, J, Tt) * 2 * B;
+                for (int x = tid; x < 2 * B; x += BS) {
+                    const int r = x / B, k = x - r * B;
+                    float v = s_col[0][r][k];
+#pragma unroll
+                    for (int w2 = 1; w2 < NW; ++w2) v += s_col[w2][r][k];
+                    dst[x] = v;
+                }
+            }
+        }
+        // row side of row tile I over this CTA's part of the row
+        const int64_t c0 = sk_cta_of(sym_row_start(I, Tt), plan.work, plan.ctas);
+        const int64_t c1 = sk_cta_of(row_end - 1, plan.work, plan.ctas);
+        double *dst = (c0 == c1) ? iside + I * 2 * B : islots + (2 * c + (I == I_first ? 0 : 1)) * 2 * B;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            dst[t * BS + tid] = acc1[t];
+            dst[B + t * BS + tid] = acc2[t];
+        }
+    }
+}
+
+// y = diag u - (row side + column sides), each row summed in a fixed order:
+// its row-side parts in CTA order, then the column sides of tile pairs (I', R)
+// for I' = 0 .. R-1.  One block per row tile R.
+template <int T>
+__global__ void __launch_bounds__(256)
+matvec_sym_finalize(const double *__restrict__ u, int64_t N, double diag1, double diag2, SymPlan plan,
+                    const double *__restrict__ islots, const double *__restrict__ iside,
+                    const float *__restrict__ jpart, double *__restrict__ y, const int *__restrict__ skip) {
+    constexpr int B = kF32Threads * T;
+    if (skip != nullptr && *((volatile const int *)skip)) return;
+    const int64_t Tt = plan.tiles;
+    const int64_t R = blockIdx.x;
+    const int64_t c0 = sk_cta_of(sym_row_start(R, Tt), plan.work, plan.ctas);
+    const int64_t c1 = sk_cta_of(sym_row_start(R + 1, Tt) - 1, plan.work, plan.ctas);
+    for (int k = threadIdx.x; k < B; k += blockDim.x) {
+        const int64_t i = R * B + k;
+        if (i >= N) break;
+        double s1 = 0.0, s2 = 0.0;
+        if (c0 == c1) {
+            s1 = iside[R * 2 * B + k];
+            s2 = iside[R * 2 * B + B + k];
+        } else {
+            for (int64_t cc = c0; cc <= c1; ++cc) {
+                const int64_t first = sym_row_of(sk_begin(cc, plan.work, plan.ctas), Tt);
+                const double *sl = islots + (2 * cc + (R == first ? 0 : 1)) * 2 * B;
+                s1 += sl[k];
+                s2 += sl[B + k];
+            }
+        }
+        for (int64_t Ip = 0; Ip < R; ++Ip) {
+            const float *jp = jpart + sym_offdiag_index(Ip, R, Tt) * 2 * B;
+            s1 += (double)jp[k];
+            s2 += (double)jp[B + k];
+        }
+        y[i] = diag1 * u[i] - s1;
+        y[N + i] = diag2 * u[N + i] - s2;
     }
 }
 
@@ -430,23 +790,51 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         prm.diag1 = diag1;
         prm.diag2 = diag2;
         const StreamKPlan &pl = ctx->plan32;
+        const bool k0 = ctx->kappa == 0.0;
+#define PB_LAUNCH_F32X2(T)                                                                                      \
+    do {                                                                                                        \
+        if (k0)                                                                                                 \
+            matvec_f32x2_kernel<T, true><<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(                   \
+                ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,    \
+                ctx->mv_count);                                                                                 \
+        else                                                                                                    \
+            matvec_f32x2_kernel<T, false><<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(                  \
+                ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,    \
+                ctx->mv_count);                                                                                 \
+    } while (0)
+#define PB_LAUNCH_SYM(T)                                                                                        \
+    do {                                                                                                        \
+        const SymPlan &sp = ctx->plansym;                                                                       \
+        constexpr int B = kF32Threads * T;                                                                      \
+        double *iside = (double *)ctx->sym_scratch;                                                             \
+        double *islots = iside + round256(sp.tiles * 2 * B * (int64_t)sizeof(double)) / sizeof(double);        \
+        float *jpart = (float *)(islots + round256(sp.ctas * 4 * B * (int64_t)sizeof(double)) / sizeof(double)); \
+        if (k0)                                                                                                 \
+            matvec_sym_kernel<T, true><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(                     \
+                ctx->pos32, ctx->nrm32, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);    \
+        else                                                                                                    \
+            matvec_sym_kernel<T, false><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(                    \
+                ctx->pos32, ctx->nrm32, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);    \
+        matvec_sym_finalize<T><<<(unsigned)sp.tiles, 256, 0, ctx->stream>>>(u, ctx->N, diag1, diag2, sp,        \
+                                                                           islots, iside, jpart, y, skip_flag); \
+        PB_LAUNCHED();                                                                                          \
+    } while (0)
+        if (f32_variant_symmetric(ctx->f32_variant) && ctx->sym_scratch == nullptr)
+            return set_error(ctx, PB_ERR_ARG, "symmetric matvec variant without its scratch");
         switch (ctx->f32_variant) {
             case MV_F32_SCALAR_T4:
                 matvec_f32_kernel<<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(
                     ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,
                     ctx->mv_count);
                 break;
-            case MV_F32_PACKED_T4:
-                matvec_f32x2_kernel<4><<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(
-                    ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,
-                    ctx->mv_count);
-                break;
-            default:
-                matvec_f32x2_kernel<2><<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(
-                    ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,
-                    ctx->mv_count);
-                break;
+            case MV_F32_PACKED_T4: PB_LAUNCH_F32X2(4); break;
+            case MV_F32_PACKED_T3: PB_LAUNCH_F32X2(3); break;
+            case MV_F32_SYM_T2: PB_LAUNCH_SYM(2); break;
+            case MV_F32_SYM_T4: PB_LAUNCH_SYM(4); break;
+            default: PB_LAUNCH_F32X2(2); break;
         }
+#undef PB_LAUNCH_F32X2
+#undef PB_LAUNCH_SYM
     } else {
         F64Params prm{ctx->eps, 1.0 / ctx->eps, ctx->kappa, diag1, diag2};
         const StreamKPlan &pl = ctx->plan64;
@@ -474,16 +862,27 @@ int matvec_occupancy(pb_precision prec) {
 }
 
 int matvec_f32_occupancy(int variant) {
+    // the kappa = 0 instantiations use fewer registers; size grids by the
+    // general one so that one plan serves both
     int n = 0;
     switch (variant) {
         case MV_F32_SCALAR_T4:
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32_kernel, kF32Threads, 0);
             break;
         case MV_F32_PACKED_T4:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<4>, kF32Threads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<4, false>, kF32Threads, 0);
+            break;
+        case MV_F32_PACKED_T3:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<3, false>, kF32Threads, 0);
+            break;
+        case MV_F32_SYM_T2:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<2, false>, kF32Threads, 0);
+            break;
+        case MV_F32_SYM_T4:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false>, kF32Threads, 0);
             break;
         default:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<2>, kF32Threads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<2, false>, kF32Threads, 0);
             break;
     }
     return n < 1 ? 1 : n;
@@ -503,13 +902,35 @@ pb_status matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm) {
     if (variant < 1 || variant > kNumF32Variants)
         return set_error(ctx, PB_ERR_ARG, "matvec variant %d is not one of 1..%d", variant, kNumF32Variants);
     if (ctas_per_sm < 0) return set_error(ctx, PB_ERR_ARG, "ctas_per_sm must be >= 0");
-    StreamKPlan pl = matvec_f32_plan(ctx, variant, ctas_per_sm);
-    if (plan_partials(pl, kF32Threads * f32_variant_targets(variant)) > ctx->partials_len ||
-        pl.target_tiles > ctx->counters_len)
-        return set_error(ctx, PB_ERR_ARG, "matvec configuration exceeds the context's scratch");
+    if (f32_variant_symmetric(variant)) {
+        int occ = matvec_f32_occupancy(variant);
+        if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
+        const int tile = kF32Threads * f32_variant_targets(variant);
+        const SymPlan sp = make_sym_plan(ctx->N, tile, (int64_t)ctx->num_sms * occ);
+        const int64_t need = sym_scratch_bytes(sp, tile);
+        if (need > ctx->sym_scratch_len) {
+            if (ctx->sym_scratch) ctx_free(ctx, ctx->sym_scratch);
+            ctx->sym_scratch = nullptr;
+            ctx->sym_scratch_len = 0;
+            pb_status s = ctx_alloc(ctx, &ctx->sym_scratch, (size_t)need, "symmetric matvec scratch");
+            if (s != PB_OK) return s;
+            ctx->sym_scratch_len = need;
+        }
+        ctx->plansym = sp;
+    } else {
+        StreamKPlan pl = matvec_f32_plan(ctx, variant, ctas_per_sm);
+        if (plan_partials(pl, kF32Threads * f32_variant_targets(variant)) > ctx->partials_len ||
+            pl.target_tiles > ctx->counters_len)
+            return set_error(ctx, PB_ERR_ARG, "matvec configuration exceeds the context's scratch");
+        ctx->plan32 = pl;
+        if (ctx->sym_scratch) {
+            ctx_free(ctx, ctx->sym_scratch);
+            ctx->sym_scratch = nullptr;
+            ctx->sym_scratch_len = 0;
+        }
+    }
     ctx->f32_variant = variant;
     ctx->f32_ctas_per_sm = ctas_per_sm;
-    ctx->plan32 = pl;
     return PB_OK;
 }
 

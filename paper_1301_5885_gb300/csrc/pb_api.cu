@@ -84,7 +84,7 @@ pb_status stage(pb_ctx *ctx, const double *src, int64_t n, double **dst, const c
 void free_all(pb_ctx *ctx) {
     void *bufs[] = {ctx->g64, ctx->pos32, ctx->nrm32, ctx->charges, ctx->b, ctx->x, ctx->partials,
                     ctx->tile_counters, ctx->red, ctx->red_counter, ctx->scalar, ctx->V, ctx->w, ctx->r,
-                    ctx->d, ctx->rres, ctx->st};
+                    ctx->d, ctx->rres, ctx->st, ctx->sym_scratch};
     for (void *p : bufs) ctx_free(ctx, p);
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
@@ -226,6 +226,7 @@ pb_status pb_create(const double *centroids, const double *normals, const double
 
     double *c_dev = nullptr, *n_dev = nullptr, *a_dev = nullptr;
     const int64_t N2 = 2 * N;
+    int sym_default = 0, sym_cps = 0;
     if (s == PB_OK) {
         // scratch sized for every kernel variant at any CTA count per SM up to
         // its occupancy (fewer CTAs never need more segments)
@@ -233,6 +234,7 @@ pb_status pb_create(const double *centroids, const double *normals, const double
         ctx->partials_len = plan_partials(ctx->plan64, kF64TargetTile);
         ctx->counters_len = ctx->plan64.target_tiles;
         for (int v = 1; v <= kNumF32Variants; ++v) {
+            if (f32_variant_symmetric(v)) continue;   // own scratch, allocated when configured
             StreamKPlan pl = matvec_f32_plan(ctx, v, 0);
             int64_t need = plan_partials(pl, kF32Threads * f32_variant_targets(v));
             if (need > ctx->partials_len) ctx->partials_len = need;
@@ -240,9 +242,15 @@ pb_status pb_create(const double *centroids, const double *normals, const double
         }
         int v = 0, cps = 0;
         default_f32_config(ctx, &v, &cps);
-        ctx->f32_variant = v;
-        ctx->f32_ctas_per_sm = cps;
-        ctx->plan32 = matvec_f32_plan(ctx, v, cps);
+        ctx->plan32 = matvec_f32_plan(ctx, MV_F32_PACKED_T2, 0);
+        ctx->f32_variant = MV_F32_PACKED_T2;
+        if (!f32_variant_symmetric(v)) {
+            ctx->f32_variant = v;
+            ctx->f32_ctas_per_sm = cps;
+            ctx->plan32 = matvec_f32_plan(ctx, v, cps);
+        }
+        sym_default = f32_variant_symmetric(v) ? v : 0;
+        sym_cps = cps;
         ctx->red_len = (int64_t)(kMaxRestart + 1) * 2 * ctx->num_sms;
     }
     if (s == PB_OK) s = ctx_alloc(ctx, (void **)&ctx->g64, 7 * N * sizeof(double), "FP64 geometry");
@@ -266,6 +274,7 @@ pb_status pb_create(const double *centroids, const double *normals, const double
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->scalar, 0, 16 * sizeof(double), ctx->stream);
         if (e != cudaSuccess) s = cuda_error(ctx, e, "counter reset");
     }
+    if (s == PB_OK && sym_default) s = matvec_configure(ctx, sym_default, sym_cps);
     if (s == PB_OK) s = stage(ctx, centroids, 3 * N, &c_dev, "centroid staging");
     if (s == PB_OK) s = stage(ctx, normals, 3 * N, &n_dev, "normal staging");
     if (s == PB_OK) s = stage(ctx, areas, N, &a_dev, "area staging");

@@ -32,9 +32,20 @@ constexpr int kF32TargetTile = kF32Threads * kF32TargetsPerThread;
 constexpr int kF32SourceTile = 256;
 // FP32-pair kernel variants (one is chosen per context, by default or by the
 // autotuner): targets per thread and scalar or packed f32x2 arithmetic.
-enum MatvecVariant { MV_F32_SCALAR_T4 = 1, MV_F32_PACKED_T2 = 2, MV_F32_PACKED_T4 = 3 };
-constexpr int kNumF32Variants = 3;
-__host__ __device__ constexpr int f32_variant_targets(int v) { return v == MV_F32_PACKED_T2 ? 2 : 4; }
+// The symmetric variants evaluate each unordered pair once for both rows.
+enum MatvecVariant {
+    MV_F32_SCALAR_T4 = 1,
+    MV_F32_PACKED_T2 = 2,
+    MV_F32_PACKED_T4 = 3,
+    MV_F32_PACKED_T3 = 4,
+    MV_F32_SYM_T2 = 5,
+    MV_F32_SYM_T4 = 6
+};
+constexpr int kNumF32Variants = 6;
+__host__ __device__ constexpr int f32_variant_targets(int v) {
+    return (v == MV_F32_PACKED_T2 || v == MV_F32_SYM_T2) ? 2 : (v == MV_F32_PACKED_T3 ? 3 : 4);
+}
+__host__ __device__ constexpr bool f32_variant_symmetric(int v) { return v == MV_F32_SYM_T2 || v == MV_F32_SYM_T4; }
 // FP64 kernel: 128 threads x 1 target, 128 sources per source tile.
 constexpr int kF64Threads = 128;
 constexpr int kF64TargetTile = kF64Threads;
@@ -59,6 +70,19 @@ __host__ __device__ inline int64_t sk_cta_of(int64_t p, int64_t W, int64_t G) {
 }
 
 StreamKPlan make_plan(int64_t n, int target_tile, int source_tile, int64_t ctas_wanted);
+
+// Split of the upper triangle of square tile pairs (I <= J, numbered row by
+// row) of the symmetric product over persistent CTAs, with the same range
+// rule as StreamKPlan.
+struct SymPlan {
+    int64_t tiles;          // square tiles of the targets
+    int64_t work;           // tiles (tiles + 1) / 2 tile pairs
+    int64_t ctas;
+};
+SymPlan make_sym_plan(int64_t n, int tile, int64_t ctas_wanted);
+// device bytes of the symmetric product's scratch (row sides, split-row
+// slots, column sides per off-diagonal tile pair)
+int64_t sym_scratch_bytes(const SymPlan &pl, int tile);
 
 // ---- GMRES device state ----------------------------------------------------
 struct GmresState {
@@ -118,6 +142,10 @@ struct pb_ctx {
     int f32_ctas_per_sm = 0;
     double *partials = nullptr;
     int64_t partials_len = 0;
+    // symmetric variants: their plan and scratch (allocated when configured)
+    pb::SymPlan plansym{};
+    void *sym_scratch = nullptr;
+    int64_t sym_scratch_len = 0;   // bytes
     unsigned int *tile_counters = nullptr;
     int64_t counters_len = 0;
 

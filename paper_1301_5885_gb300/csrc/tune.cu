@@ -71,7 +71,7 @@ pb_status pb_matvec_get_config(pb_ctx *ctx, int *variant, int *ctas_per_sm, int6
     if (!ctx) return set_error(nullptr, PB_ERR_ARG, "pb_matvec_get_config: NULL context");
     if (variant) *variant = ctx->f32_variant;
     if (ctas_per_sm) *ctas_per_sm = ctx->f32_ctas_per_sm;
-    if (ctas) *ctas = ctx->plan32.ctas;
+    if (ctas) *ctas = f32_variant_symmetric(ctx->f32_variant) ? ctx->plansym.ctas : ctx->plan32.ctas;
     return PB_OK;
 }
 

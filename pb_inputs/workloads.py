@@ -107,15 +107,30 @@ def gaussian_value_and_grad(pos: np.ndarray, radii: np.ndarray, beta: float = 2.
 
 
 def solute_surface(pos: np.ndarray, radii: np.ndarray, spacing: float, beta: float = 2.0,
-                   relax_iterations: int = 8) -> Surface:
+                   relax_iterations: int = 8, analytic_normals: bool = True) -> Surface:
     """Isosurface at level 1 of the summed atom Gaussians, relaxed on the exact
-    level set."""
+    level set.
+
+    With ``analytic_normals`` every element's normal is the unit outward normal
+    of the smooth surface at its centroid, -grad f / |grad f|, instead of the
+    flat facet's normal.  Near pinch points of the level set the piecewise
+    linear surface folds, and facet normals there point inward; such elements
+    make the collocation system stagnate under restarted GMRES, while the
+    smooth-surface normals keep every element consistently oriented."""
     margin = float(radii.max()) * 2.0 + 2.0 * spacing
     origin = pos.min(0) - margin
     shape = tuple(int(np.ceil(e / spacing)) + 1 for e in (pos.max(0) + margin - origin))
     field = gaussian_density(pos, radii, origin, spacing, shape, beta=beta)
-    return isosurface(field, origin, spacing, 1.0, value_and_grad=gaussian_value_and_grad(pos, radii, beta),
-                      relax_iterations=relax_iterations)
+    fg = gaussian_value_and_grad(pos, radii, beta)
+    surf = isosurface(field, origin, spacing, 1.0, value_and_grad=fg, relax_iterations=relax_iterations)
+    if analytic_normals:
+        _, g = fg(surf.centroids)
+        gn = np.linalg.norm(g, axis=1, keepdims=True)
+        ok = gn[:, 0] > 0
+        nrm = surf.normals.copy()
+        nrm[ok] = -g[ok] / gn[ok]
+        surf = Surface(surf.centroids, np.ascontiguousarray(nrm), surf.areas, surf.vertices, surf.faces)
+    return surf
 
 
 PROBE_RADIUS = 1.4

@@ -77,7 +77,7 @@ def test_matvec_fp64_matches_oracle(name, surf, kappa):
     assert np.max(np.abs(y - ref)) <= 1e-9 * np.max(np.abs(ref))
 
 
-F32_VARIANTS = [1, 2, 3]   # scalar T4, packed f32x2 T2, packed f32x2 T4
+F32_VARIANTS = [1, 2, 3, 4, 5, 6]   # scalar T4, packed f32x2 T2, T4, T3, symmetric T2, T4
 
 
 @pytest.mark.parametrize("name,surf", SURFACES, ids=[s[0] for s in SURFACES])
@@ -106,6 +106,30 @@ def test_matvec_fp32pair_small_grids_match_oracle(variant, ctas_per_sm):
     assert np.linalg.norm(y - ref) <= 2e-5 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("variant", [5, 6])
+@pytest.mark.parametrize("ctas_per_sm", [1, 3])
+@pytest.mark.parametrize("kappa", [0.1257, 0.0])
+def test_symmetric_matvec_rows_split_over_ctas(variant, ctas_per_sm, kappa):
+    """More tile pairs than CTAs: CTA ranges cross row tiles, so rows are
+    split over several CTAs (their partial row sides meet in the finishing
+    kernel) and CTAs hold whole rows in between."""
+    surf = pi.icosphere(8.0, 5)
+    surf = surf.subset(np.arange(surf.n - 123))      # ragged last tile
+    u = _u(surf.n, 13)
+    pb = _pb()
+    with _ctx(surf, kappa=kappa) as ctx:
+        pb.pb_matvec_configure(ctx, variant, ctas_per_sm)
+        assert pb.pb_matvec_get_config(ctx)["variant"] == variant
+        y1 = _gpu_matvec(ctx, u, "fp32pair")
+        y2 = _gpu_matvec(ctx, u, "fp32pair")
+        pb.pb_matvec_configure(ctx, 3, 0)
+        y3 = _gpu_matvec(ctx, u, "fp32pair")
+    ref = oracle.matvec(surf, 80.0, kappa, u)
+    assert np.array_equal(y1, y2)                     # fixed summation order
+    assert np.linalg.norm(y1 - ref) <= 2e-5 * np.linalg.norm(ref)
+    assert np.linalg.norm(y1 - y3) <= 2e-5 * np.linalg.norm(ref)
+
+
 def test_autotune_picks_a_valid_variant_with_the_same_result():
     pb = _pb()
     surf = pi.icosphere(8.0, 5)
@@ -123,7 +147,7 @@ def test_autotune_picks_a_valid_variant_with_the_same_result():
             pb.pb_matvec_configure(ctx, 7, 0)
 
 
-@pytest.mark.parametrize("prec,variant", [("fp64", 0), ("fp32pair", 1), ("fp32pair", 2), ("fp32pair", 3)])
+@pytest.mark.parametrize("prec,variant", [("fp64", 0)] + [("fp32pair", v) for v in F32_VARIANTS])
 def test_matvec_is_identity_without_jump_or_salt(prec, variant):
     surf = pi.icosphere(2.0, 3)
     u = _u(surf.n, 3)
@@ -143,7 +167,7 @@ def test_single_element_has_only_the_diagonal(prec):
     assert y[1] == 0.5 * (1 + 1 / 80.0) * -1.3
 
 
-@pytest.mark.parametrize("prec,variant", [("fp64", 0), ("fp32pair", 1), ("fp32pair", 2), ("fp32pair", 3)])
+@pytest.mark.parametrize("prec,variant", [("fp64", 0)] + [("fp32pair", v) for v in F32_VARIANTS])
 def test_duplicate_centroids_are_dropped_like_the_self_term(prec, variant):
     base = pi.icosphere(2.0, 2)
     idx = np.concatenate([np.arange(base.n), [7, 7, 100]])
@@ -306,3 +330,19 @@ def test_geometry_info_and_translation_invariance():
         ea = pb.pb_solve(a, tol=1e-7, prec="fp32pair").energy_kcal
         eb = pb.pb_solve(b, tol=1e-7, prec="fp32pair").energy_kcal
     assert eb == pytest.approx(ea, rel=1e-5)       # FP32 coordinates are centred first
+
+
+@pytest.mark.parametrize("variant", F32_VARIANTS)
+@pytest.mark.parametrize("kappa", [0.1257, 0.0])
+def test_matvec_large_inputs_stay_finite(variant, kappa):
+    """Inputs of size 1e6 (beyond anything GMRES feeds the product, whose
+    vectors are unit-norm) give finite, correct rows: the self-pair clamp
+    never forms an infinity."""
+    surf = pi.icosphere(3.0, 3)
+    u = _u(surf.n, 14) * 1e6
+    with _ctx(surf, kappa=kappa) as ctx:
+        _pb().pb_matvec_configure(ctx, variant, 0)
+        y = _gpu_matvec(ctx, u, "fp32pair")
+    ref = oracle.matvec(surf, 80.0, kappa, u)
+    assert np.all(np.isfinite(y))
+    assert np.linalg.norm(y - ref) <= 2e-5 * np.linalg.norm(ref)
