@@ -431,7 +431,7 @@ def _clock_and_uuid(torch, dev):
     return ClockSampler(uuid)
 
 
-BATCH_FP32_OPS_PER_EVAL = 37     # K1..K4 of one pair, scalar FP32 (2 MUFU besides)
+BATCH_FP32_OPS_PER_EVAL = 36     # K1..K4 of one pair, packed FP32 (kappa > 0; 2 MUFU besides)
 BATCH_FP32_OPS_PER_RHS = 4       # the two rows' accumulations per charge set
 
 

@@ -248,8 +248,9 @@ void pb_server_destroy(pb_server *sv);
  * Eqs. (12)-(13) evaluated once for both of its rows, using K1(i,j) = K1(j,i),
  * K4(i,j) = K4(j,i) and the sign change of c_x, c_y under the exchange; two
  * kernel launches per product; device scratch of about 4 N^2 / (128 t) bytes,
- * t the targets per thread, allocated when the variant is configured and
- * freed when another is; PB_ERR_OOM if it cannot be allocated); 0 = the
+ * t the targets per thread, allocated by the first product that uses the
+ * variant and freed when another variant is configured; that product returns
+ * PB_ERR_OOM if it cannot be allocated); 0 = the
  * stored or built-in default.  The packed variants use a kappa = 0
  * specialisation when the context's kappa is 0.  ctas_per_sm: resident CTAs
  * per SM of the persistent grid, 0 = as many as fit.  Results differ between

@@ -31,8 +31,11 @@
 
 namespace pb {
 
-constexpr int kBThreads = 128;          // product kernel: one target per thread
-constexpr int kBSourceTile = 128;
+constexpr int kBThreads = 128;          // product kernel threads
+constexpr int kBSourceTile = 256;       // sources per staged tile (one pair per thread)
+// targets per thread of the product kernel for R right-hand sides (more
+// targets share each staged source when fewer accumulators are needed)
+__host__ __device__ constexpr int bmatvec_targets(int R) { return R <= 1 ? 4 : (R <= 4 ? 2 : 1); }
 constexpr int kChunk = 4096;            // vector chunk (elements) of the GMRES kernels
 constexpr int kVThreads = 256;
 constexpr int LDH = kMaxRestart + 1;
@@ -88,16 +91,110 @@ __device__ __forceinline__ int find_surface(const BSurf *surf, int nsurf, int64_
     return lo;
 }
 
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_dup(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// One staged tile of source pairs against the thread's T targets, for the R
+// right-hand sides of the surface.  Packed f32x2: each instruction does a
+// step of two pairs (one target, two sources).  The target normals arrive
+// negated so that no operand needs a sign change: with c_x' = -c_x, n' = -n,
+// 1 - e' = 1 - e (1 + kappa rho) and -b (b the K3 factor),
+//   K1 = (1 - e)/rho,  K2 = a c_y,  K3 = (-b) c_x',
+//   K4 = (-e3 c_x c_y / rho^2 + (e' - 1) n) / rho^3 = ((e3 c_x' c_y) / rho^2 + (1 - e') n') / rho^3
+// with a = (eps e' - 1)/rho^3 and e3 = e (3 + 3 kappa rho + kappa^2 rho^2) - 3:
+// 36 FP32 operations per pair for K1..K4 and 4 per right-hand side.  With
+// kappa = 0 (K0), K1 = K4 = 0 and the constant factors of K2, K3 are folded
+// into the staged weights: 16 operations per pair and 2 per right-hand side.
+// The self pair is removed by the clamps on 1/rho and 1/rho^2 (every term an
+// exact zero, as in the single-surface kernels).
+template <int R, int T, bool K0>
+__device__ __forceinline__ void bstage(const float4 *s_g, const float4 *s_w, int npairs, float eps, float inv_eps,
+                                       float kappa, float nk, const float2 (&xi)[T], const float2 (&yi)[T],
+                                       const float2 (&zi)[T], const float2 (&nxi)[T], const float2 (&nyi)[T],
+                                       const float2 (&nzi)[T], float2 (&f1)[R][T], float2 (&f2)[R][T]) {
+    constexpr int TQ = kBSourceTile / 2;
+    const float2 nk2 = p_dup(nk), mkap2 = p_dup(-kappa), one2 = p_dup(1.f), mone2 = p_dup(-1.f);
+    const float2 three2 = p_dup(3.f), mthree2 = p_dup(-3.f), meps2 = p_dup(-eps), epsm1 = p_dup(eps - 1.f);
+    const float2 ieps2 = p_dup(inv_eps), omieps = p_dup(1.f - inv_eps);
+#pragma unroll 1
+    for (int q = 0; q < npairs; ++q) {
+        const float4 A = s_g[q], Bq = s_g[TQ + q], C = s_g[2 * TQ + q];
+        const float2 mx = make_float2(A.x, A.y), my = make_float2(A.z, A.w), mz = make_float2(Bq.x, Bq.y);
+        const float2 snx = make_float2(Bq.z, Bq.w), sny = make_float2(C.x, C.y), snz = make_float2(C.z, C.w);
+        float4 w[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) w[r] = s_w[r * TQ + q];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const float2 dx = p_add(xi[t], mx), dy = p_add(yi[t], my), dz = p_add(zi[t], mz);
+            const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
+            float2 inv, inv2;
+            inv.x = fminf(rsqrt_approx(r2.x), 1e9f);
+            inv.y = fminf(rsqrt_approx(r2.y), 1e9f);
+            if (K0) {
+                inv2 = p_mul(inv, inv);
+            } else {
+                inv2.x = fminf(rcp_approx(r2.x), 1e18f);
+                inv2.y = fminf(rcp_approx(r2.y), 1e18f);
+            }
+            const float2 inv3 = p_mul(inv2, inv);
+            const float2 ncx = p_fma(dx, nxi[t], p_fma(dy, nyi[t], p_mul(dz, nzi[t])));   // -c_x
+            const float2 cy = p_fma(dx, snx, p_fma(dy, sny, p_mul(dz, snz)));
+            if (K0) {
+                const float2 k2 = p_mul(cy, inv3), k3 = p_mul(ncx, inv3);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    f1[r][t] = p_fma(k2, make_float2(w[r].z, w[r].w), f1[r][t]);
+                    f2[r][t] = p_fma(k3, make_float2(w[r].x, w[r].y), f2[r][t]);
+                }
+            } else {
+                const float2 rho = p_mul(r2, inv);
+                const float2 arg = p_mul(nk2, rho);
+                float2 e;
+                e.x = exp2_approx(arg.x);
+                e.y = exp2_approx(arg.y);
+                const float2 mkr = p_mul(mkap2, rho);
+                const float2 nnn = p_fma(nxi[t], snx, p_fma(nyi[t], sny, p_mul(nzi[t], snz)));   // -n
+                const float2 ome = p_fma(e, mone2, one2);
+                const float2 ome1 = p_fma(e, mkr, ome);                                   // 1 - e (1 + kappa rho)
+                const float2 k1 = p_mul(ome, inv);
+                const float2 k2 = p_mul(p_mul(p_fma(ome1, meps2, epsm1), inv3), cy);
+                const float2 k3 = p_mul(p_mul(p_fma(ome1, ieps2, omieps), inv3), ncx);
+                const float2 p3 = p_fma(mkr, p_add(mkr, mthree2), three2);
+                const float2 e3 = p_fma(e, p3, mthree2);
+                const float2 ccy = p_mul(p_mul(e3, ncx), cy);
+                const float2 k4 = p_mul(p_fma(ccy, inv2, p_mul(ome1, nnn)), inv3);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float2 wpsi = make_float2(w[r].x, w[r].y), wphi = make_float2(w[r].z, w[r].w);
+                    f1[r][t] = p_fma(k1, wpsi, p_fma(k2, wphi, f1[r][t]));
+                    f2[r][t] = p_fma(k3, wpsi, p_fma(k4, wphi, f2[r][t]));
+                }
+            }
+        }
+    }
+}
+
 // y_q = A u_q for every instance q; u_q = x_q (usel 0) or V_q[k] (usel 1), y_q = w_q.
+// CTA c owns the flattened (surface, target tile, source tile) range
+// [c W / G, (c+1) W / G); a target tile split over several CTAs is finished
+// by the last to arrive, which adds the partial rows in CTA order.
 template <int R>
 __global__ void __launch_bounds__(kBThreads)
 bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restrict__ inst, int64_t W, int64_t G,
                int usel, int k, const int *__restrict__ active, double *__restrict__ partials,
                unsigned int *__restrict__ counters, unsigned long long *__restrict__ evaluated) {
-    constexpr int TT = kBThreads, TS = kBSourceTile;
-    __shared__ float4 s_pos[TS];
-    __shared__ float4 s_nrm[TS];
-    __shared__ float2 s_w[R][TS];        // (W dphi, W phi) / (4 pi) per right-hand side
+    constexpr int BS = kBThreads, T = bmatvec_targets(R), TT = BS * T, TS = kBSourceTile, TQ = TS / 2;
+    static_assert(TQ == BS, "one source pair per thread when staging");
+    __shared__ float4 s_g[3 * TQ];       // {-x0,-x1,-y0,-y1}, {-z0,-z1,nx0,nx1}, {ny0,ny1,nz0,nz1}
+    __shared__ float4 s_w[R * TQ];       // per right-hand side {W dphi0, W dphi1, W phi0, W phi1} / (4 pi)
     __shared__ const double *s_u[R];
     __shared__ double *s_y[R];
     __shared__ int s_last;
@@ -137,63 +234,70 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
                 s_y[tid] = nullptr;
             }
         }
-        const int64_t i = a * TT + tid;
-        const int64_t ic = i < N ? i : N - 1;
-        const float4 qi = sf.pos[ic], ni = sf.nrm[ic];
-        double acc1[R], acc2[R];
+        const bool k0 = sf.kappa == 0.f;
+        // kappa = 0: (eps - 1) and (1/eps - 1) folded into the weights (K3 uses -c_x)
+        const float wphi_scale = k0 ? sf.eps - 1.f : 1.f, wpsi_scale = k0 ? 1.f - sf.inv_eps : 1.f;
+        float2 xi[T], yi[T], zi[T], nxi[T], nyi[T], nzi[T];
 #pragma unroll
-        for (int r = 0; r < R; ++r) { acc1[r] = 0.0; acc2[r] = 0.0; }
+        for (int t = 0; t < T; ++t) {
+            const int64_t i = a * TT + t * BS + tid;
+            const int64_t ic = i < N ? i : N - 1;
+            const float4 q = sf.pos[ic], n = sf.nrm[ic];
+            xi[t] = p_dup(q.x); yi[t] = p_dup(q.y); zi[t] = p_dup(q.z);
+            nxi[t] = p_dup(-n.x); nyi[t] = p_dup(-n.y); nzi[t] = p_dup(-n.z);
+        }
+        double acc1[R][T], acc2[R][T];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int t = 0; t < T; ++t) { acc1[r][t] = 0.0; acc2[r][t] = 0.0; }
 
         for (int64_t st = s_first; st < s_end; ++st) {
             __syncthreads();
             {
-                const int64_t j = st * TS + tid;
-                if (j < N) {
-                    const float4 q = sf.pos[j], n = sf.nrm[j];
-                    s_pos[tid] = q;
-                    s_nrm[tid] = n;
+                // stage source pair (2 tid, 2 tid + 1); a missing second source
+                // repeats the first with zero weights
+                const int64_t j0 = st * TS + 2 * tid;
+                if (j0 < N) {
+                    const bool has1 = j0 + 1 < N;
+                    const int64_t j1 = has1 ? j0 + 1 : j0;
+                    const float4 p0 = sf.pos[j0], p1 = sf.pos[j1], n0 = sf.nrm[j0], n1 = sf.nrm[j1];
+                    s_g[tid] = make_float4(-p0.x, -p1.x, -p0.y, -p1.y);
+                    s_g[TQ + tid] = make_float4(-p0.z, -p1.z, n0.x, n1.x);
+                    s_g[2 * TQ + tid] = make_float4(n0.y, n1.y, n0.z, n1.z);
+                    const float w0 = p0.w, w1 = has1 ? p1.w : 0.f;
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         const double *u = s_u[r];
-                        s_w[r][tid] = u ? make_float2((float)u[N + j] * q.w, (float)u[j] * q.w) : make_float2(0.f, 0.f);
+                        s_w[r * TQ + tid] = u ? make_float4((float)u[N + j0] * (w0 * wpsi_scale),
+                                                            (float)u[N + j1] * (w1 * wpsi_scale),
+                                                            (float)u[j0] * (w0 * wphi_scale),
+                                                            (float)u[j1] * (w1 * wphi_scale))
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
             }
             __syncthreads();
-            const int cnt = (int)((N - st * TS) < TS ? (N - st * TS) : TS);
-            float f1[R], f2[R];
+            const int64_t rem = N - st * TS;
+            const int npairs = (int)(((rem < TS) ? rem : TS) + 1) / 2;
+            float2 f1[R][T], f2[R][T];
 #pragma unroll
-            for (int r = 0; r < R; ++r) { f1[r] = 0.f; f2[r] = 0.f; }
-            for (int jj = 0; jj < cnt; ++jj) {
-                const float4 sp = s_pos[jj];
-                const float4 sn = s_nrm[jj];
-                const float dx = qi.x - sp.x, dy = qi.y - sp.y, dz = qi.z - sp.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float inv = fminf(rsqrt_approx(r2), 1e12f);   // self pair: every term exactly 0
-                const float rho = r2 * inv;
-                const float e = exp2_approx(sf.nk * rho);
-                const float kr = sf.kappa * rho;
-                const float e1 = fmaf(e, kr, e);
-                const float inv2 = inv * inv;
-                const float inv3 = inv2 * inv;
-                const float cx = fmaf(dx, ni.x, fmaf(dy, ni.y, dz * ni.z));
-                const float cy = fmaf(dx, sn.x, fmaf(dy, sn.y, dz * sn.z));
-                const float nn = fmaf(ni.x, sn.x, fmaf(ni.y, sn.y, ni.z * sn.z));
-                const float k1 = (1.f - e) * inv;
-                const float k2 = fmaf(sf.eps, e1, -1.f) * cy * inv3;
-                const float k3 = fmaf(e1, sf.inv_eps, -1.f) * cx * inv3;
-                const float p3 = fmaf(kr, kr + 3.f, 3.f);
-                const float e3 = fmaf(e, p3, -3.f);
-                const float k4 = fmaf(-e3 * cx * cy, inv2, fmaf(e1, nn, -nn)) * inv3;
+            for (int r = 0; r < R; ++r)
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const float2 w = s_w[r][jj];
-                    f1[r] = fmaf(k1, w.x, fmaf(k2, w.y, f1[r]));
-                    f2[r] = fmaf(k3, w.x, fmaf(k4, w.y, f2[r]));
+                for (int t = 0; t < T; ++t) { f1[r][t] = p_dup(0.f); f2[r][t] = p_dup(0.f); }
+            if (k0)
+                bstage<R, T, true>(s_g, s_w, npairs, sf.eps, sf.inv_eps, sf.kappa, sf.nk, xi, yi, zi, nxi, nyi, nzi,
+                                   f1, f2);
+            else
+                bstage<R, T, false>(s_g, s_w, npairs, sf.eps, sf.inv_eps, sf.kappa, sf.nk, xi, yi, zi, nxi, nyi, nzi,
+                                    f1, f2);
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    acc1[r][t] += (double)f1[r][t].x + (double)f1[r][t].y;
+                    acc2[r][t] += (double)f2[r][t].x + (double)f2[r][t].y;
                 }
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) { acc1[r] += (double)f1[r]; acc2[r] += (double)f2[r]; }
         }
 
         const int64_t p_tile0 = sf.work_base + a * S;
@@ -201,12 +305,16 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
         const int nseg = (int)(c1 - c0 + 1);
         const int64_t gtile = sf.tile_base + a;
         if (nseg == 1) {
-            if (i < N) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (s_y[r]) {
-                        s_y[r][i] = sf.diag1 * s_u[r][i] - acc1[r];
-                        s_y[r][N + i] = sf.diag2 * s_u[r][N + i] - acc2[r];
+            for (int t = 0; t < T; ++t) {
+                const int64_t i = a * TT + t * BS + tid;
+                if (i < N) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if (s_y[r]) {
+                            s_y[r][i] = sf.diag1 * s_u[r][i] - acc1[r][t];
+                            s_y[r][N + i] = sf.diag2 * s_u[r][N + i] - acc2[r][t];
+                        }
                     }
                 }
             }
@@ -214,37 +322,43 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
             const int64_t slot = 2 * c + (gtile == first_tile ? 0 : 1);
             double *mine = partials + slot * (2 * R * TT);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                mine[(2 * r) * TT + tid] = acc1[r];
-                mine[(2 * r + 1) * TT + tid] = acc2[r];
-            }
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    mine[(2 * r) * TT + t * BS + tid] = acc1[r][t];
+                    mine[(2 * r + 1) * TT + t * BS + tid] = acc2[r][t];
+                }
             __threadfence();
             __syncthreads();
             if (tid == 0) s_last = (atomicAdd(&counters[gtile], 1u) == (unsigned int)(nseg - 1));
             __syncthreads();
             if (s_last) {
                 __threadfence();
-                double s1[R], s2[R];
 #pragma unroll
-                for (int r = 0; r < R; ++r) { s1[r] = 0.0; s2[r] = 0.0; }
-                for (int o = 0; o < nseg; ++o) {
-                    const int64_t co = c0 + o;
-                    const int64_t pb0 = sk_begin(co, W, G);
-                    const int sc = find_surface(surf, nsurf, pb0);
-                    const int64_t ft = surf[sc].tile_base + (pb0 - surf[sc].work_base) / surf[sc].S;
-                    const double *pp = partials + (2 * co + (gtile == ft ? 0 : 1)) * (2 * R * TT);
+                for (int t = 0; t < T; ++t) {
+                    double s1[R], s2[R];
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        s1[r] += __ldcg(pp + (2 * r) * TT + tid);
-                        s2[r] += __ldcg(pp + (2 * r + 1) * TT + tid);
+                    for (int r = 0; r < R; ++r) { s1[r] = 0.0; s2[r] = 0.0; }
+                    for (int o = 0; o < nseg; ++o) {
+                        const int64_t co = c0 + o;
+                        const int64_t pb0 = sk_begin(co, W, G);
+                        const int sc = find_surface(surf, nsurf, pb0);
+                        const int64_t ft = surf[sc].tile_base + (pb0 - surf[sc].work_base) / surf[sc].S;
+                        const double *pp = partials + (2 * co + (gtile == ft ? 0 : 1)) * (2 * R * TT);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            s1[r] += __ldcg(pp + (2 * r) * TT + t * BS + tid);
+                            s2[r] += __ldcg(pp + (2 * r + 1) * TT + t * BS + tid);
+                        }
                     }
-                }
-                if (i < N) {
+                    const int64_t i = a * TT + t * BS + tid;
+                    if (i < N) {
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        if (s_y[r]) {
-                            s_y[r][i] = sf.diag1 * s_u[r][i] - s1[r];
-                            s_y[r][N + i] = sf.diag2 * s_u[r][N + i] - s2[r];
+                        for (int r = 0; r < R; ++r) {
+                            if (s_y[r]) {
+                                s_y[r][i] = sf.diag1 * s_u[r][i] - s1[r];
+                                s_y[r][N + i] = sf.diag2 * s_u[r][N + i] - s2[r];
+                            }
                         }
                     }
                 }
@@ -631,6 +745,10 @@ pb_status Engine::rebuild() {
     surf_member_.clear();
     int64_t tiles = 0, work = 0;
     int rmax = 1;
+    for (EngineMember *mb : members_)
+        if (!mb->finished && mb->nrhs > rmax) rmax = mb->nrhs;
+    R_ = rmax <= 1 ? 1 : (rmax <= 2 ? 2 : (rmax <= 4 ? 4 : 8));
+    const int64_t TT = (int64_t)kBThreads * bmatvec_targets(R_);
     for (size_t mi = 0; mi < members_.size(); ++mi) {
         EngineMember *mb = members_[mi];
         if (mb->finished) continue;
@@ -645,7 +763,7 @@ pb_status Engine::rebuild() {
         sf.nk = (float)(-c->kappa * 1.4426950408889634);
         sf.diag1 = 0.5 * (1.0 + c->eps);
         sf.diag2 = 0.5 * (1.0 + 1.0 / c->eps);
-        const int64_t T = (c->N + kBThreads - 1) / kBThreads;
+        const int64_t T = (c->N + TT - 1) / TT;
         sf.S = (c->N + kBSourceTile - 1) / kBSourceTile;
         sf.tile_base = tiles;
         sf.work_base = work;
@@ -653,7 +771,6 @@ pb_status Engine::rebuild() {
         sf.nrhs = mb->nrhs;
         tiles += T;
         work += T * sf.S;
-        rmax = mb->nrhs > rmax ? mb->nrhs : rmax;
         const int64_t n2 = 2 * c->N;
         const size_t per = (size_t)(m_ + 5) * n2;
         for (int r = 0; r < mb->nrhs; ++r) {
@@ -681,7 +798,6 @@ pb_status Engine::rebuild() {
     nchunks_ = (int)hch.size();
     tiles_ = tiles;
     W_ = work;
-    R_ = rmax <= 1 ? 1 : (rmax <= 2 ? 2 : (rmax <= 4 ? 4 : 8));
     rhs_width = R_;
     if (gexec_) cudaGraphExecDestroy(gexec_);
     if (graph_) cudaGraphDestroy(graph_);
@@ -715,7 +831,7 @@ pb_status Engine::rebuild() {
         s = grow((void **)&act_ax_, &c2, cap_flags_, sizeof(int), "engine flags");
     }
     if (s == PB_OK) s = grow((void **)&red_, &cap_red_, (size_t)(m_ + 1) * nchunks_, sizeof(double), "engine reductions");
-    if (s == PB_OK) s = grow((void **)&part_, &cap_part_, (size_t)2 * G_ * 2 * R_ * kBThreads, sizeof(double), "engine partials");
+    if (s == PB_OK) s = grow((void **)&part_, &cap_part_, (size_t)2 * G_ * 2 * R_ * TT, sizeof(double), "engine partials");
     if (s == PB_OK && !scalar_) {
         cudaError_t e = cudaMallocAsync((void **)&scalar_, 64 * sizeof(double), stream_);
         if (e != cudaSuccess) s = cuda_fail(e, "engine scalars");

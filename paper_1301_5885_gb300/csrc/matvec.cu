@@ -773,6 +773,19 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
     const double diag1 = 0.5 * (1.0 + ctx->eps), diag2 = 0.5 * (1.0 + 1.0 / ctx->eps);
     if (prec != PB_FP32PAIR && prec != PB_FP64)
         return set_error(ctx, PB_ERR_ARG, "pb_matvec: unknown precision %d", (int)prec);
+    if (prec == PB_FP32PAIR && f32_variant_symmetric(ctx->f32_variant)) {
+        // the symmetric variants' scratch, allocated by the first product that needs it
+        const int64_t need = sym_scratch_bytes(ctx->plansym, kF32Threads * f32_variant_targets(ctx->f32_variant));
+        if (need > ctx->sym_scratch_len) {
+            if (ctx->sym_scratch) ctx_free(ctx, ctx->sym_scratch);
+            ctx->device_bytes -= ctx->sym_scratch_len;
+            ctx->sym_scratch = nullptr;
+            ctx->sym_scratch_len = 0;
+            pb_status s = ctx_alloc(ctx, &ctx->sym_scratch, (size_t)need, "symmetric matvec scratch");
+            if (s != PB_OK) return s;
+            ctx->sym_scratch_len = need;
+        }
+    }
     const bool timed = ctx->prof_on;
     if (timed) {
         if (ctx->prof_used + 2 > (int)ctx->prof_ev.size()) {
@@ -819,8 +832,6 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
                                                                            islots, iside, jpart, y, skip_flag); \
         PB_LAUNCHED();                                                                                          \
     } while (0)
-        if (f32_variant_symmetric(ctx->f32_variant) && ctx->sym_scratch == nullptr)
-            return set_error(ctx, PB_ERR_ARG, "symmetric matvec variant without its scratch");
         switch (ctx->f32_variant) {
             case MV_F32_SCALAR_T4:
                 matvec_f32_kernel<<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(
@@ -906,17 +917,8 @@ pb_status matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm) {
         int occ = matvec_f32_occupancy(variant);
         if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
         const int tile = kF32Threads * f32_variant_targets(variant);
-        const SymPlan sp = make_sym_plan(ctx->N, tile, (int64_t)ctx->num_sms * occ);
-        const int64_t need = sym_scratch_bytes(sp, tile);
-        if (need > ctx->sym_scratch_len) {
-            if (ctx->sym_scratch) ctx_free(ctx, ctx->sym_scratch);
-            ctx->sym_scratch = nullptr;
-            ctx->sym_scratch_len = 0;
-            pb_status s = ctx_alloc(ctx, &ctx->sym_scratch, (size_t)need, "symmetric matvec scratch");
-            if (s != PB_OK) return s;
-            ctx->sym_scratch_len = need;
-        }
-        ctx->plansym = sp;
+        // the scratch is allocated by the first product that needs it
+        ctx->plansym = make_sym_plan(ctx->N, tile, (int64_t)ctx->num_sms * occ);
     } else {
         StreamKPlan pl = matvec_f32_plan(ctx, variant, ctas_per_sm);
         if (plan_partials(pl, kF32Threads * f32_variant_targets(variant)) > ctx->partials_len ||
@@ -925,6 +927,7 @@ pb_status matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm) {
         ctx->plan32 = pl;
         if (ctx->sym_scratch) {
             ctx_free(ctx, ctx->sym_scratch);
+            ctx->device_bytes -= ctx->sym_scratch_len;
             ctx->sym_scratch = nullptr;
             ctx->sym_scratch_len = 0;
         }

@@ -15,12 +15,16 @@
 namespace pb {
 namespace {
 
-// Built-in default, from timings on GB300: packed f32x2 with 4 targets per
-// thread is fastest once there are enough target tiles to fill the GPU
-// (798 vs 795 Gpairs/s at N = 81,920; the scalar kernel gives 627); below
-// that the 2-target variant keeps more CTAs busy (512 vs 400 Gpairs/s at
-// N = 5,120).
-constexpr int64_t kPackedT4MinN = 32768;
+// Built-in default, from timings on GB300 (ordered pairs per second): the
+// symmetric kernel with 4 targets per thread is fastest once the upper
+// triangle of 512-point tile pairs fills the GPU (1168 Gpairs/s at
+// N = 81,920 and 1190 at N = 327,680, against 790 for the packed kernel and
+// 627 for the scalar one; 2212 against 1672 with kappa = 0); with 2 targets
+// per thread it reaches 1041.  Small surfaces have too few tile pairs for
+// either: at N = 5,120 the packed 2-target kernel gives 505 Gpairs/s, the
+// symmetric ones 400 and 241.
+constexpr int64_t kSymT4MinN = 40960;
+constexpr int64_t kSymT2MinN = 16384;
 constexpr int kBuckets = 256;
 
 struct TuneEntry {
@@ -46,7 +50,7 @@ void default_f32_config(pb_ctx *ctx, int *variant, int *ctas_per_sm) {
         *variant = e.variant;
         *ctas_per_sm = e.ctas_per_sm;
     } else {
-        *variant = ctx->N >= kPackedT4MinN ? MV_F32_PACKED_T4 : MV_F32_PACKED_T2;
+        *variant = ctx->N >= kSymT4MinN ? MV_F32_SYM_T4 : (ctx->N >= kSymT2MinN ? MV_F32_SYM_T2 : MV_F32_PACKED_T2);
         *ctas_per_sm = 0;
     }
 }

@@ -42,7 +42,10 @@ def test_surface_potential_error_and_order(prec):
     ek = oracle.kirkwood_energy(pi.helix_charges(), 4.0, 1.0, 80.0, 0.0)
     for lvl in levels:
         p = pi.helix_sphere(level=lvl)
-        x, e = _solve(p, prec, 1e-9)
+        # FP32-pair products put a floor of about 1e-9 under the relative
+        # residual (it depends on the kernel variant), far below the
+        # discretisation error measured here
+        x, e = _solve(p, prec, 1e-9 if prec == "fp64" else 1e-7)
         phi_ex, _ = oracle.kirkwood_surface(p.surface.centroids, p.charges, 4.0, p.eps1, p.eps2, p.kappa)
         ephi.append(oracle.error_linf(x[:p.n], phi_ex))
         energies.append(abs(e - ek) / abs(ek))
