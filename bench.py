@@ -52,6 +52,7 @@ MATVEC_KERNELS = {
     4: ("matvec_f32x2_kernel<3>", 39, 18),
     5: ("matvec_sym_kernel<2> + matvec_sym_finalize<2>", 23, 10),
     6: ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", 23, 10),
+    7: ("matvec_sym_kernel<4> (4 CTAs/SM) + matvec_sym_finalize<4>", 23, 10),
 }
 
 
@@ -85,11 +86,14 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["solve", "batch", "serve"], default="solve",
-                    help="solve: one molecule per step (default); batch: 64 solutes x 8 charge sets per step; "
-                         "serve: Poisson request stream through the solve server")
+    ap.add_argument("--mode", choices=["solve", "matvec", "batch", "serve"], default="solve",
+                    help="solve: one molecule per step (default); matvec: one FP32-pair product per step; "
+                         "batch: 64 solutes x 8 charge sets per step; serve: Poisson request stream through "
+                         "the solve server")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="matvec mode: FP32-pair kernel variant (0: the library's default for N)")
     ap.add_argument("--n-solutes", type=int, default=64, help="batch mode: solutes per batch")
-    ap.add_argument("--requests", type=int, default=48, help="serve mode: requests in the stream")
+    ap.add_argument("--requests", type=int, default=200, help="serve mode: requests in the stream")
     ap.add_argument("--pool", type=int, default=8, help="serve mode: distinct solutes the requests draw from")
     ap.add_argument("--gen-workers", type=int, default=0, help="processes generating solute meshes (0: auto)")
     return ap.parse_args()
@@ -435,6 +439,65 @@ BATCH_FP32_OPS_PER_EVAL = 36     # K1..K4 of one pair, packed FP32 (kappa > 0; 2
 BATCH_FP32_OPS_PER_RHS = 4       # the two rows' accumulations per charge set
 
 
+def run_matvec(args):
+    """The product alone: y = A u for a fixed random u, one launch per step,
+    timed with CUDA events on the context's stream (median over steps)."""
+    import numpy as np
+    import torch
+    import paper_1301_5885_gb300 as pb
+    import pb_inputs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    prob = pb_inputs.by_name(args.workload)
+    s = prob.surface
+    stream = torch.cuda.current_stream()
+    ctx = pb.pb_create(s.centroids, s.normals, s.areas, prob.charges, prob.eps1, prob.eps2, prob.kappa,
+                       stream=stream)
+    if args.variant:
+        pb.pb_matvec_configure(ctx, args.variant, 0)
+    cfg = pb.pb_matvec_get_config(ctx)
+    gen = torch.Generator(device=dev).manual_seed(7)
+    u = torch.randn(2 * prob.n, dtype=torch.float64, device=dev, generator=gen)
+    y = torch.empty_like(u)
+    for _ in range(args.warmup):
+        pb.pb_matvec(ctx, u, y, "fp32pair")
+    torch.cuda.synchronize()
+    sampler = _clock_and_uuid(torch, dev)
+    sampler.start()
+    l0 = pb.pb_kernel_launches()
+    evs = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pb.pb_matvec(ctx, u, y, "fp32pair")
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    launches = pb.pb_kernel_launches() - l0
+    clocks = sampler.stop()
+    pb.pb_destroy(ctx)
+    ms = np.array([a.elapsed_time(b) for a, b in evs])
+    pairs = prob.n * (prob.n - 1)
+    value = pairs / (np.median(ms) * 1e-3) / 1e9
+    kname, ops_k, ops_0 = MATVEC_KERNELS[cfg["variant"]]
+    ops = ops_0 if prob.kappa == 0.0 else ops_k
+    peak = matvec_peak_gpairs(ops)
+    line = {"metric": "matvec Gpairs/s", "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.median(ms)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs, f64 accumulation", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_triangles": prob.n,
+                       "variant": cfg["variant"], "ctas": cfg["ctas"],
+                       "l2": "inputs L2-resident by design (the product is FP32-pipe bound)"},
+            "roofline": {"kernel": kname, "bound": "alu", "achieved": value, "peak": peak, "unit": UNIT,
+                         "frac": value / peak, "traffic": MATVEC_TRAFFIC_BYTES.get((kname, args.workload)),
+                         "peak_basis": f"FP32 pipe: {SMS} SMs x 128 lanes x {SM_MAX_MHZ:.0f} MHz / {ops} FP32 ops "
+                                       "per ordered pair (derived)"},
+            "ms_min": float(ms.min()), "ms_max": float(ms.max()), "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch(args):
     import numpy as np
     import pb_inputs
@@ -614,6 +677,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "matvec":
+        return run_matvec(args)
     if args.mode == "batch":
         return run_batch(args)
     if args.mode == "serve":

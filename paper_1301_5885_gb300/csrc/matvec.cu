@@ -533,8 +533,8 @@ __device__ __forceinline__ void sym_stage(const float4 *s_a, const float4 *s_b, 
     }
 }
 
-template <int T, bool K0>
-__global__ void __launch_bounds__(kF32Threads, T >= 4 ? 3 : 4)
+template <int T, bool K0, int MINB>
+__global__ void __launch_bounds__(kF32Threads, MINB)
 matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm, const double *__restrict__ u,
                   int64_t N, F32Params prm, SymPlan plan, double *__restrict__ islots, double *__restrict__ iside,
                   float *__restrict__ jpart, const int *__restrict__ skip, unsigned long long *__restrict__ evaluated) {
@@ -680,11 +680,28 @@ matvec_sym_finalize(const double *__restrict__ u, int64_t N, double diag1, doubl
                 s2 += sl[B + k];
             }
         }
-        for (int64_t Ip = 0; Ip < R; ++Ip) {
-            const float *jp = jpart + sym_offdiag_index(Ip, R, Tt) * 2 * B;
-            s1 += (double)jp[k];
-            s2 += (double)jp[B + k];
+        // column sides: four interleaved partial sums (I' mod 4), added in a
+        // fixed order, so that the loads and FP64 adds overlap
+        double a1[4] = {0.0, 0.0, 0.0, 0.0}, a2[4] = {0.0, 0.0, 0.0, 0.0};
+        int64_t Ip = 0;
+        for (; Ip + 4 <= R; Ip += 4) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float *jp = jpart + sym_offdiag_index(Ip + v, R, Tt) * 2 * B;
+                a1[v] += (double)jp[k];
+                a2[v] += (double)jp[B + k];
+            }
         }
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            if (Ip + v < R) {
+                const float *jp = jpart + sym_offdiag_index(Ip + v, R, Tt) * 2 * B;
+                a1[v] += (double)jp[k];
+                a2[v] += (double)jp[B + k];
+            }
+        }
+        s1 += (a1[0] + a1[1]) + (a1[2] + a1[3]);
+        s2 += (a2[0] + a2[1]) + (a2[2] + a2[3]);
         y[i] = diag1 * u[i] - s1;
         y[N + i] = diag2 * u[N + i] - s2;
     }
@@ -815,7 +832,7 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
                 ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,    \
                 ctx->mv_count);                                                                                 \
     } while (0)
-#define PB_LAUNCH_SYM(T)                                                                                        \
+#define PB_LAUNCH_SYM(T, MINB)                                                                                      \
     do {                                                                                                        \
         const SymPlan &sp = ctx->plansym;                                                                       \
         constexpr int B = kF32Threads * T;                                                                      \
@@ -823,10 +840,10 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         double *islots = iside + round256(sp.tiles * 2 * B * (int64_t)sizeof(double)) / sizeof(double);        \
         float *jpart = (float *)(islots + round256(sp.ctas * 4 * B * (int64_t)sizeof(double)) / sizeof(double)); \
         if (k0)                                                                                                 \
-            matvec_sym_kernel<T, true><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(                     \
+            matvec_sym_kernel<T, true, MINB><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(               \
                 ctx->pos32, ctx->nrm32, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);    \
         else                                                                                                    \
-            matvec_sym_kernel<T, false><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(                    \
+            matvec_sym_kernel<T, false, MINB><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(              \
                 ctx->pos32, ctx->nrm32, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);    \
         matvec_sym_finalize<T><<<(unsigned)sp.tiles, 256, 0, ctx->stream>>>(u, ctx->N, diag1, diag2, sp,        \
                                                                            islots, iside, jpart, y, skip_flag); \
@@ -840,8 +857,9 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
                 break;
             case MV_F32_PACKED_T4: PB_LAUNCH_F32X2(4); break;
             case MV_F32_PACKED_T3: PB_LAUNCH_F32X2(3); break;
-            case MV_F32_SYM_T2: PB_LAUNCH_SYM(2); break;
-            case MV_F32_SYM_T4: PB_LAUNCH_SYM(4); break;
+            case MV_F32_SYM_T2: PB_LAUNCH_SYM(2, 4); break;
+            case MV_F32_SYM_T4: PB_LAUNCH_SYM(4, 3); break;
+            case MV_F32_SYM_T4_O4: PB_LAUNCH_SYM(4, 4); break;
             default: PB_LAUNCH_F32X2(2); break;
         }
 #undef PB_LAUNCH_F32X2
@@ -887,10 +905,13 @@ int matvec_f32_occupancy(int variant) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<3, false>, kF32Threads, 0);
             break;
         case MV_F32_SYM_T2:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<2, false>, kF32Threads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<2, false, 4>, kF32Threads, 0);
             break;
         case MV_F32_SYM_T4:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false>, kF32Threads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false, 3>, kF32Threads, 0);
+            break;
+        case MV_F32_SYM_T4_O4:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false, 4>, kF32Threads, 0);
             break;
         default:
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<2, false>, kF32Threads, 0);

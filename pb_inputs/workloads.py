@@ -106,23 +106,47 @@ def gaussian_value_and_grad(pos: np.ndarray, radii: np.ndarray, beta: float = 2.
     return fg
 
 
+SOLUTE_LEVELS = (1.0, 0.95, 1.05, 0.9, 1.1)
+
+
+def _folded_facets(surf: Surface, value_and_grad) -> int:
+    """Facets whose geometric normal opposes the smooth surface's normal
+    (-grad f) at their centroid."""
+    v = surf.vertices[surf.faces]
+    fn = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    _, g = value_and_grad(surf.centroids)
+    return int(np.sum(np.einsum("ij,ij->i", fn, -g) <= 0.0))
+
+
 def solute_surface(pos: np.ndarray, radii: np.ndarray, spacing: float, beta: float = 2.0,
-                   relax_iterations: int = 8, analytic_normals: bool = True) -> Surface:
-    """Isosurface at level 1 of the summed atom Gaussians, relaxed on the exact
-    level set.
+                   relax_iterations: int = 8, analytic_normals: bool = True,
+                   levels=SOLUTE_LEVELS) -> Surface:
+    """Isosurface of the summed atom Gaussians, relaxed on the exact level set.
+
+    The level is the first of ``levels`` (1 first) whose triangulation has no
+    folded facet, else the one with the fewest: where a critical value of the
+    field lies close to the level, the level set has a pinch finer than the
+    grid and the piecewise-linear surface folds there; a slightly different
+    level moves off it.
 
     With ``analytic_normals`` every element's normal is the unit outward normal
     of the smooth surface at its centroid, -grad f / |grad f|, instead of the
-    flat facet's normal.  Near pinch points of the level set the piecewise
-    linear surface folds, and facet normals there point inward; such elements
-    make the collocation system stagnate under restarted GMRES, while the
-    smooth-surface normals keep every element consistently oriented."""
+    flat facet's normal; the two agree on an unfolded mesh up to the facet's
+    tilt."""
     margin = float(radii.max()) * 2.0 + 2.0 * spacing
     origin = pos.min(0) - margin
     shape = tuple(int(np.ceil(e / spacing)) + 1 for e in (pos.max(0) + margin - origin))
     field = gaussian_density(pos, radii, origin, spacing, shape, beta=beta)
     fg = gaussian_value_and_grad(pos, radii, beta)
-    surf = isosurface(field, origin, spacing, 1.0, value_and_grad=fg, relax_iterations=relax_iterations)
+    best, best_folds = None, None
+    for level in levels:
+        cand = isosurface(field, origin, spacing, level, value_and_grad=fg, relax_iterations=relax_iterations)
+        folds = _folded_facets(cand, fg)
+        if best is None or folds < best_folds:
+            best, best_folds = cand, folds
+        if folds == 0:
+            break
+    surf = best
     if analytic_normals:
         _, g = fg(surf.centroids)
         gn = np.linalg.norm(g, axis=1, keepdims=True)
@@ -137,21 +161,26 @@ PROBE_RADIUS = 1.4
 
 
 def protein_like(n_atoms: int = 2000, seed: int = 3, target_triangles: int | None = 300_000,
-                 spacing: float | None = None, beta: float = 1.0, probe: float = PROBE_RADIUS) -> Problem:
+                 spacing: float | None = None, beta: float = 0.4, probe: float = PROBE_RADIUS) -> Problem:
     """Seeded protein-like solute.
 
     The surface is the level-1 set of summed Gaussians whose radii are the atom
     radii plus a solvent-probe radius (1.4 A), so that crevices narrower than a
     water molecule are filled, as on a probe-traced molecular surface (Section 1).
     Without the probe the bead-chain surface has thin necks between atoms and
-    the collocation system converges very slowly.  With ``target_triangles`` the
-    grid spacing is chosen from a coarse trial surface so that the final
-    triangle count lands near the target (the count scales like area / spacing^2)."""
+    the collocation system converges very slowly.  The soft Gaussians
+    (beta = 0.4) keep the surface's curvature resolved at the coarse grid
+    spacings (up to about 2 A) that 40 triangles per atom need: with beta = 1
+    such meshes had folded facets, facets whose orientation opposes the smooth
+    surface's, and some of them stalled restarted GMRES.  With
+    ``target_triangles`` the grid spacing is chosen from a coarse trial surface
+    so that the final triangle count lands near the target (the count scales
+    like area / spacing^2)."""
     pos, radii, q = compact_chain(n_atoms, seed)
     rs = radii + probe
     if spacing is None:
         trial = 1.2
-        n_trial = solute_surface(pos, rs, trial, beta, relax_iterations=0).n
+        n_trial = solute_surface(pos, rs, trial, beta, relax_iterations=0, levels=(1.0,)).n
         spacing = trial * np.sqrt(n_trial / float(target_triangles))
     surf = solute_surface(pos, rs, spacing, beta, relax_iterations=10)
     ch = np.concatenate([pos, q[:, None]], 1)

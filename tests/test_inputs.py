@@ -44,6 +44,21 @@ def test_solute_isosurface_is_closed_oriented_and_encloses_its_atoms():
     assert abs(round(p.charges[:, 3].sum()) - p.charges[:, 3].sum()) < 1e-12
 
 
+def test_coarse_solute_mesh_has_no_folded_facets():
+    """At about 40 triangles per atom (grid spacing near 1.9 A) every facet is
+    oriented like the smooth surface through it: its geometric normal makes an
+    acute angle with -grad f at its centroid (the element normal)."""
+    p = pi.protein_like(n_atoms=150, seed=1010, target_triangles=6000)
+    s = p.surface
+    v = s.vertices[s.faces]
+    fn = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    fn /= np.linalg.norm(fn, axis=1)[:, None]
+    cos = np.einsum("ij,ij->i", fn, s.normals)
+    assert cos.min() > 0.2
+    h = np.sqrt(s.areas.mean())
+    assert s.areas.min() > 0.02 * h * h
+
+
 def test_generators_are_deterministic():
     a = pi.ball_charges(20, 16.0, 2)
     b = pi.ball_charges(20, 16.0, 2)

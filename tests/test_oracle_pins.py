@@ -118,7 +118,7 @@ def test_dense_assembly_and_lu_match_matrix_free_gmres(which):
     if which == "sphere":
         p = pi.kirkwood_sphere_multi(level=2, radius=4.0, n_charges=3, seed=1)
     else:
-        p = pi.protein_like(n_atoms=6, seed=2, target_triangles=None, spacing=2.8)
+        p = pi.protein_like(n_atoms=6, seed=2, target_triangles=None, spacing=3.2)
     assert p.n <= 700
     eps = p.eps2 / p.eps1
     A = oracle.assemble(p.surface, eps, p.kappa)
