@@ -570,6 +570,8 @@ bg_update_x(const BChunk *__restrict__ ch, const BInst *__restrict__ inst) {
 }
 
 // per-surface activity flags for the product, and x_is_zero bookkeeping
+// act_*: 1 when a surface's product is needed (read by the batched product);
+// act_*[nsurf + s] holds the negation (the skip flag of a single-surface product).
 __global__ void bg_flags(const BSurf *__restrict__ surf, int nsurf, const BInst *__restrict__ inst, int *act_step,
                          int *act_ax, int clear_x_zero) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -584,6 +586,8 @@ __global__ void bg_flags(const BSurf *__restrict__ surf, int nsurf, const BInst 
     }
     act_step[s] = step;
     act_ax[s] = ax;
+    act_step[nsurf + s] = !step;
+    act_ax[nsurf + s] = !ax;
 }
 
 __global__ void bg_status(const BInst *__restrict__ inst, int nq, BStatus *out) {
@@ -743,6 +747,7 @@ pb_status Engine::rebuild() {
     std::vector<BInst> hq;
     std::vector<BChunk> hch;
     surf_member_.clear();
+    direct_.clear();
     int64_t tiles = 0, work = 0;
     int rmax = 1;
     for (EngineMember *mb : members_)
@@ -763,8 +768,13 @@ pb_status Engine::rebuild() {
         sf.nk = (float)(-c->kappa * 1.4426950408889634);
         sf.diag1 = 0.5 * (1.0 + c->eps);
         sf.diag2 = 0.5 * (1.0 + 1.0 / c->eps);
-        const int64_t T = (c->N + TT - 1) / TT;
+        // a single charge set on a context whose product is the symmetric
+        // kernel: its own launch of that kernel (about 23 FP32 operations per
+        // ordered pair against 40 in the batched kernel); no batched work
+        const bool direct = mb->nrhs == 1 && f32_variant_symmetric(c->f32_variant);
+        const int64_t T = direct ? 0 : (c->N + TT - 1) / TT;
         sf.S = (c->N + kBSourceTile - 1) / kBSourceTile;
+        if (direct) direct_.push_back((int)hs.size());
         sf.tile_base = tiles;
         sf.work_base = work;
         sf.inst0 = (int)hq.size();
@@ -816,6 +826,14 @@ pb_status Engine::rebuild() {
     G_ = (int64_t)num_sms_ * occ;
     if (G_ > W_) G_ = W_;
     ctas = G_;
+    for (int si : direct_) {
+        pb_ctx *c = members_[surf_member_[si]]->surf;
+        const cudaStream_t keep_stream = c->stream;
+        c->stream = stream_;
+        pb_status ps = matvec_prepare(c);
+        c->stream = keep_stream;
+        if (ps != PB_OK) return fail(ps, "engine: %s", c->last_error);
+    }
     pb_status s = PB_OK;
     if (s == PB_OK) s = grow((void **)&d_surf_, &cap_surf_, nsurf_, sizeof(BSurf), "engine surfaces");
     if (s == PB_OK) s = grow((void **)&d_inst_, &cap_inst_, nq_, sizeof(BInst), "engine instances");
@@ -823,7 +841,7 @@ pb_status Engine::rebuild() {
     if (s == PB_OK) s = grow((void **)&cnt_inst_, &cap_cnt_inst_, nq_, sizeof(unsigned int), "engine counters");
     if (s == PB_OK) s = grow((void **)&cnt_tile_, &cap_cnt_tile_, tiles_, sizeof(unsigned int), "engine counters");
     if (s == PB_OK) s = grow((void **)&evals_, &cap_evals_, nsurf_, sizeof(unsigned long long), "engine counters");
-    if (s == PB_OK) s = grow((void **)&act_step_, &cap_flags_, nsurf_, sizeof(int), "engine flags");
+    if (s == PB_OK) s = grow((void **)&act_step_, &cap_flags_, 2 * (size_t)nsurf_, sizeof(int), "engine flags");
     if (s == PB_OK) {
         size_t c2 = 0;
         if (act_ax_) cudaFreeAsync(act_ax_, stream_);
@@ -874,18 +892,41 @@ void Engine::enqueue_cycle() {
     const int sb = (nsurf_ + 127) / 128, qb = (nq_ + 127) / 128;
     auto mv = [&](int usel, int k, const int *act) {
         if (timing_ && ev_used_ + 2 <= (int)ev_.size()) cudaEventRecord(ev_[ev_used_], stream_);
-        switch (R_) {
-            case 1: bmatvec_kernel<1><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
-            case 2: bmatvec_kernel<2><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
-            case 4: bmatvec_kernel<4><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
-            default: bmatvec_kernel<8><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
+        if (W_ > 0) {
+            switch (R_) {
+                case 1: bmatvec_kernel<1><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
+                case 2: bmatvec_kernel<2><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
+                case 4: bmatvec_kernel<4><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
+                default: bmatvec_kernel<8><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
+            }
+            ++cycle_kernels_;
+            ++cycle_mv_;
+        }
+        // single-surface symmetric products; their skip flag is the negated
+        // activity flag, and their evaluation counter the engine's
+        for (int si : direct_) {
+            EngineMember *mb = members_[surf_member_[si]];
+            pb_ctx *c = mb->surf;
+            const int64_t n2 = 2 * c->N;
+            const double *u = usel ? mb->vec + 4 * n2 + (int64_t)k * n2 : mb->vec + n2;   // V[k] or x
+            double *y = mb->vec + 2 * n2;                                                  // w
+            const cudaStream_t keep_stream = c->stream;
+            unsigned long long *keep_count = c->mv_count;
+            const bool keep_prof = c->prof_on;
+            c->stream = stream_;
+            c->mv_count = evals_ + si;
+            c->prof_on = false;
+            matvec_launch(c, u, y, PB_FP32PAIR, act + nsurf_ + si);
+            c->stream = keep_stream;
+            c->mv_count = keep_count;
+            c->prof_on = keep_prof;
+            cycle_kernels_ += 2;
+            ++cycle_mv_;
         }
         if (timing_ && ev_used_ + 2 <= (int)ev_.size()) {
             cudaEventRecord(ev_[ev_used_ + 1], stream_);
             ev_used_ += 2;
         }
-        ++cycle_kernels_;
-        ++cycle_mv_;
     };
     mv(0, 0, act_ax_);
     bg_cycle_start<<<nchunks_, kVThreads, 0, stream_>>>(1, d_ch_, d_inst_, red_, cnt_inst_);

@@ -84,6 +84,7 @@ class Engine {
     int nsurf_ = 0, nq_ = 0, nchunks_ = 0, R_ = 1;
     int64_t W_ = 0, G_ = 0, tiles_ = 0;
     std::vector<int> surf_member_;     // table surface -> member index
+    std::vector<int> direct_;          // table surfaces with their own symmetric product
     BSurf *d_surf_ = nullptr;
     BInst *d_inst_ = nullptr;
     BChunk *d_ch_ = nullptr;

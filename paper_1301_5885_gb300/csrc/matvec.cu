@@ -790,18 +790,10 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
     const double diag1 = 0.5 * (1.0 + ctx->eps), diag2 = 0.5 * (1.0 + 1.0 / ctx->eps);
     if (prec != PB_FP32PAIR && prec != PB_FP64)
         return set_error(ctx, PB_ERR_ARG, "pb_matvec: unknown precision %d", (int)prec);
-    if (prec == PB_FP32PAIR && f32_variant_symmetric(ctx->f32_variant)) {
+    if (prec == PB_FP32PAIR) {
         // the symmetric variants' scratch, allocated by the first product that needs it
-        const int64_t need = sym_scratch_bytes(ctx->plansym, kF32Threads * f32_variant_targets(ctx->f32_variant));
-        if (need > ctx->sym_scratch_len) {
-            if (ctx->sym_scratch) ctx_free(ctx, ctx->sym_scratch);
-            ctx->device_bytes -= ctx->sym_scratch_len;
-            ctx->sym_scratch = nullptr;
-            ctx->sym_scratch_len = 0;
-            pb_status s = ctx_alloc(ctx, &ctx->sym_scratch, (size_t)need, "symmetric matvec scratch");
-            if (s != PB_OK) return s;
-            ctx->sym_scratch_len = need;
-        }
+        pb_status s = matvec_prepare(ctx);
+        if (s != PB_OK) return s;
     }
     const bool timed = ctx->prof_on;
     if (timed) {
@@ -928,6 +920,20 @@ StreamKPlan matvec_f32_plan(pb_ctx *ctx, int variant, int ctas_per_sm) {
 
 int64_t plan_partials(const StreamKPlan &pl, int target_tile) {
     return pl.target_tiles * pl.max_segments * 2 * target_tile;
+}
+
+pb_status matvec_prepare(pb_ctx *ctx) {
+    if (!f32_variant_symmetric(ctx->f32_variant)) return PB_OK;
+    const int64_t need = sym_scratch_bytes(ctx->plansym, kF32Threads * f32_variant_targets(ctx->f32_variant));
+    if (need <= ctx->sym_scratch_len) return PB_OK;
+    if (ctx->sym_scratch) ctx_free(ctx, ctx->sym_scratch);
+    ctx->device_bytes -= ctx->sym_scratch_len;
+    ctx->sym_scratch = nullptr;
+    ctx->sym_scratch_len = 0;
+    pb_status s = ctx_alloc(ctx, &ctx->sym_scratch, (size_t)need, "symmetric matvec scratch");
+    if (s != PB_OK) return s;
+    ctx->sym_scratch_len = need;
+    return PB_OK;
 }
 
 pb_status matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm) {

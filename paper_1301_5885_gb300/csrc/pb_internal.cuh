@@ -211,8 +211,14 @@ StreamKPlan matvec_f32_plan(pb_ctx *ctx, int variant, int ctas_per_sm);
 // partial-row capacity (doubles) a plan needs
 int64_t plan_partials(const StreamKPlan &pl, int target_tile);
 pb_status matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm);
+// allocates the scratch the configured FP32 variant needs (on ctx->stream), so
+// that later products allocate nothing (for example inside a stream capture)
+pb_status matvec_prepare(pb_ctx *ctx);
 // tune.cu: the stored or built-in FP32 kernel choice for this context's size
 void default_f32_config(pb_ctx *ctx, int *variant, int *ctas_per_sm);
+// device scratch of the built-in default product for n points (an estimate
+// for admission control; the symmetric variants' scratch, else 0)
+int64_t default_scratch_bytes(int64_t n, int num_sms);
 
 // pb_api.cu: fold recorded matvec event pairs into ctx->prof_ms (syncs the stream)
 pb_status profile_flush(pb_ctx *ctx);

@@ -72,9 +72,9 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 // Estimated device bytes of one request: its context (geometry in FP64 and
 // FP32, right-hand side and solution, matvec scratch) plus the engine member
 // (Krylov basis and work vectors).
-int64_t footprint(int64_t N, int64_t Nc, int m) {
+int64_t footprint(int64_t N, int64_t Nc, int m, int num_sms) {
     const int64_t ctx_bytes = N * (7 * 8 + 2 * 16 + 4 * 8) + Nc * 32 + ((int64_t)4 << 20);
-    return ctx_bytes + Engine::member_bytes(N, 1, m) + Nc * 32;
+    return ctx_bytes + default_scratch_bytes(N, num_sms) + Engine::member_bytes(N, 1, m) + Nc * 32;
 }
 
 void finish(pb_server *sv, Request *r, int status, double energy, int iters) {
@@ -249,7 +249,7 @@ pb_status pb_server_submit(pb_server *sv, const double *centroids, const double 
     r->eps1 = eps1;
     r->eps2 = eps2;
     r->kappa = kappa;
-    r->bytes = footprint(N, Nc, sv->opts.restart);
+    r->bytes = footprint(N, Nc, sv->opts.restart, sv->num_sms);
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lock(sv->mu);

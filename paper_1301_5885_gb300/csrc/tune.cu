@@ -43,6 +43,13 @@ int bucket_of(int64_t n) {
 
 }  // namespace
 
+int64_t default_scratch_bytes(int64_t n, int num_sms) {
+    const int v = n >= kSymT4MinN ? MV_F32_SYM_T4 : (n >= kSymT2MinN ? MV_F32_SYM_T2 : 0);
+    if (v == 0) return 0;
+    const int tile = kF32Threads * f32_variant_targets(v);
+    return sym_scratch_bytes(make_sym_plan(n, tile, (int64_t)num_sms * 4), tile);
+}
+
 void default_f32_config(pb_ctx *ctx, int *variant, int *ctas_per_sm) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     const TuneEntry &e = g_tune[ctx->device & 7][bucket_of(ctx->N)];

@@ -27,10 +27,13 @@ def _pb():
 
 
 def _mix():
-    """Uneven surfaces, 1..8 charge sets each, kappa in {0, 0.1257}."""
+    """Uneven surfaces, 1..8 charge sets each, kappa in {0, 0.1257}.  The
+    20,480-triangle surfaces with one charge set take their own symmetric
+    product (their contexts default to it), the rest share the batched one."""
     out = []
     for k, (lvl, rad, nq, nr, kap) in enumerate([(2, 3.0, 3, 1, 0.1257), (3, 5.0, 6, 4, 0.0),
-                                                (4, 8.0, 10, 8, 0.1257), (3, 6.0, 5, 3, 0.1257)]):
+                                                (4, 8.0, 10, 8, 0.1257), (3, 6.0, 5, 3, 0.1257),
+                                                (5, 12.0, 8, 1, 0.0), (5, 14.0, 6, 1, 0.1257)]):
         p = pi.kirkwood_sphere_multi(level=lvl, radius=rad, n_charges=nq, seed=30 + k, kappa=kap)
         sets = pi.charge_variants(p.charges, nr, seed=40 + k, frac=0.3)
         out.append((p, sets))
