@@ -52,7 +52,6 @@ MATVEC_KERNELS = {
     4: ("matvec_f32x2_kernel<3>", 39, 18),
     5: ("matvec_sym_kernel<2> + matvec_sym_finalize<2>", 23, 10),
     6: ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", 23, 10),
-    7: ("matvec_sym_kernel<4> (4 CTAs/SM) + matvec_sym_finalize<4>", 23, 10),
 }
 
 
@@ -81,7 +80,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sphere2")
     ap.add_argument("--prec", choices=["fp32pair", "fp64"], default="fp32pair")
-    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--tol", type=float, default=None,
+                    help="GMRES relative-residual tolerance (default 1e-4 for solve, 1e-6 for batch and serve, "
+                         "where the protein-like surfaces need it for a 1e-5 energy error)")
     ap.add_argument("--restart", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -619,10 +620,12 @@ def run_serve(args):
         l0 = pb.pb_kernel_launches()
         t_start = time.perf_counter()
 
+        req_key = {}
+
         def feeder():
             for g, k, kk in zip(gaps, picks, kaps):
                 time.sleep(float(g))
-                submit(sv, int(k), kappas[int(kk)])
+                req_key[submit(sv, int(k), kappas[int(kk)])] = (int(k), int(kk))
         th = threading.Thread(target=feeder)
         th.start()
         th.join()
@@ -650,6 +653,15 @@ def run_serve(args):
                         t = time.perf_counter()
                         pb.pb_solve(ctx, tol=args.tol, prec="fp64", raise_on_noconv=False)
                         seq64[(k, kk)] = time.perf_counter() - t
+    # FP64 reference energies (tight tolerance, untimed) for the small solutes
+    ref64 = {}
+    for key in seq64:
+        k, kk = key
+        c, n, a, q = pool[k]
+        with pb.pb_create(c, n, a, q, 1.0, 80.0, kappas[kk]) as ctx:
+            ref64[key] = pb.pb_solve(ctx, tol=1e-10, maxit=3000, prec="fp64").energy_kcal
+    errs = [abs(r["energy_kcal"] - ref64[key]) / abs(ref64[key])
+            for r, key in ((r, req_key.get(r["id"])) for r in res) if key in ref64]
     t32 = sum(seq32[(int(k), int(kk))] for k, kk in zip(picks, kaps))
     sub = [(int(k), int(kk)) for k, kk in zip(picks, kaps) if (int(k), int(kk)) in seq64]
     line = {"metric": METRIC, "value": products / wall / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.requests,
@@ -664,6 +676,8 @@ def run_serve(args):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(lat.mean())},
             "all_converged": ok, "max_active_seen": st1["max_active_seen"],
+            "rel_energy_err": {"max_vs_fp64_gpu_small_subset": max(errs) if errs else None,
+                               "results_compared": len(errs)},
             "baselines": {"sequential_fp32_solves_per_s": args.requests / t32,
                           "sequential_fp64_solves_per_s_small_subset": (len(sub) / sum(seq64[x] for x in sub))
                           if sub else None,
@@ -675,6 +689,8 @@ def run_serve(args):
 
 def main():
     args = parse()
+    if args.tol is None:
+        args.tol = 1e-6 if args.mode in ("batch", "serve") else 1e-4
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "matvec":

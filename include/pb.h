@@ -244,8 +244,7 @@ void pb_server_destroy(pb_server *sv);
  * paper has a single FP64 kernel).  variant: 1 = scalar FP32, 4 targets per
  * thread; 2 = packed f32x2, 2 targets per thread; 3 = packed f32x2, 4 targets
  * per thread; 4 = packed f32x2, 3 targets per thread; 5 and 6 = symmetric
- * packed f32x2 with 2 and 4 targets per thread, 7 = as 6 but compiled for
- * four resident CTAs per SM (each unordered pair of
+ * packed f32x2 with 2 and 4 targets per thread (each unordered pair of
  * Eqs. (12)-(13) evaluated once for both of its rows, using K1(i,j) = K1(j,i),
  * K4(i,j) = K4(j,i) and the sign change of c_x, c_y under the exchange; two
  * kernel launches per product; device scratch of about 4 N^2 / (128 t) bytes,

@@ -425,34 +425,45 @@ __host__ __device__ inline int64_t sym_offdiag_index(int64_t I, int64_t J, int64
     return sym_row_start(I, tiles) + (J - I) - I - 1;
 }
 
-// Sums four values g1 = (A, B), g2 = (C, D) over the warp: lanes 0-7 end with
-// the total of A, 8-15 of B, 16-23 of C, 24-31 of D.
-__device__ __forceinline__ float reduce_scatter4(float2 g1, float2 g2) {
-    const int lane = threadIdx.x & 31;
-    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
-    float2 keep = hi16 ? g2 : g1;
-    const float2 send = hi16 ? g1 : g2;
-    keep.x += __shfl_xor_sync(0xffffffffu, send.x, 16);
-    keep.y += __shfl_xor_sync(0xffffffffu, send.y, 16);
-    float k = hi8 ? keep.y : keep.x;
-    const float o = hi8 ? keep.x : keep.y;
-    k += __shfl_xor_sync(0xffffffffu, o, 8);
-    k += __shfl_xor_sync(0xffffffffu, k, 4);
-    k += __shfl_xor_sync(0xffffffffu, k, 2);
-    k += __shfl_xor_sync(0xffffffffu, k, 1);
-    return k;
-}
-
 struct SymConsts {
     float2 nk2, mkap2, one2, mone2, mthree2, three2, meps2, epsm1, ieps2, omieps;
+};
+
+// The warp reduce-scatter of four values (lanes 0-7 end with the total of the
+// first, 8-15 of the second, 16-23 of the third, 24-31 of the fourth), cut
+// into steps so that its shuffles can be interleaved with independent work:
+// begin() exchanges halves across lanes 16 apart, step(1..4) finishes the
+// previous exchange and starts the next (8, 4, 2, 1 lanes apart), end()
+// adds the last one.  6 shuffles in all.
+struct WarpReduce4 {
+    float2 keep, recv;
+    float k, o;
+    __device__ __forceinline__ void begin(float2 g1, float2 g2, bool hi16) {
+        keep = hi16 ? g2 : g1;
+        const float2 send = hi16 ? g1 : g2;
+        recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+        recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+    }
+    __device__ __forceinline__ void step(int st, bool hi8) {
+        if (st == 1) {
+            keep.x += recv.x;
+            keep.y += recv.y;
+            k = hi8 ? keep.y : keep.x;
+            o = __shfl_xor_sync(0xffffffffu, hi8 ? keep.x : keep.y, 8);
+        } else {
+            k += o;
+            o = __shfl_xor_sync(0xffffffffu, k, st == 2 ? 4 : (st == 3 ? 2 : 1));
+        }
+    }
+    __device__ __forceinline__ float end() { return k + o; }
 };
 
 // One staged source tile against the thread's T targets: the row sides into
 // f1, f2 and, with COL, the column sides of each source pair reduced over the
 // warp into col (lanes 0-7: f1 side of the pair's first source, 8-15 of its
 // second, 16-23 and 24-31: f2 side; col[k] and col[B + k] for source k of the
-// tile).  The reduction of pair q is issued after the arithmetic of pair
-// q + 1 so that its shuffle chain overlaps that work.
+// tile).  The reduction of pair q runs during the arithmetic of pair q + 1,
+// one shuffle step after each target, so that its latency is hidden.
 template <int T, bool K0, bool COL>
 __device__ __forceinline__ void sym_stage(const float4 *s_a, const float4 *s_b, const float4 *s_c,
                                           const float4 *s_d, int npairs, const float2 (&xi)[T],
@@ -462,7 +473,11 @@ __device__ __forceinline__ void sym_stage(const float4 *s_a, const float4 *s_b, 
                                           const SymConsts &k) {
     constexpr int B = kF32Threads * T;
     const int lane = threadIdx.x & 31;
-    float2 pg1 = p_dup(0.f), pg2 = p_dup(0.f);
+    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+    // this lane's slot for a reduced pair q: col[cbase + 2 q]
+    const int cbase = (lane >> 4) * B + ((lane >> 3) & 1);
+    const bool writer = (lane & 7) == 0;
+    WarpReduce4 red;
     for (int q = 0; q < npairs; ++q) {
         const float4 A = s_a[q], Bq = s_b[q], C = s_c[q], D = s_d[q];
         const float2 mx = make_float2(A.x, A.y), my = make_float2(A.z, A.w), mz = make_float2(Bq.x, Bq.y);
@@ -517,19 +532,31 @@ __device__ __forceinline__ void sym_stage(const float4 *s_a, const float4 *s_b, 
                     g2 = p_fma(p_mul(nb, cy), wpi[t], p_fma(k4, wfi[t], g2));
                 }
             }
+            // one step of the previous pair's reduction per target (T >= 2)
+            if (COL && q > 0) {
+                if (T == 2) {
+                    if (t == 0) { red.step(1, hi8); red.step(2, hi8); }
+                    else { red.step(3, hi8); red.step(4, hi8); }
+                } else if (t < 4) {
+                    red.step(t + 1, hi8);
+                }
+            }
         }
         if (COL) {
             if (q > 0) {
-                const float tot = reduce_scatter4(pg1, pg2);
-                if ((lane & 7) == 0) col[(lane >> 4) * B + 2 * (q - 1) + ((lane >> 3) & 1)] = tot;
+                const float tot = red.end();
+                if (writer) col[cbase + 2 * (q - 1)] = tot;
             }
-            pg1 = g1;
-            pg2 = g2;
+            red.begin(g1, g2, hi16);
         }
     }
     if (COL && npairs > 0) {
-        const float tot = reduce_scatter4(pg1, pg2);
-        if ((lane & 7) == 0) col[(lane >> 4) * B + 2 * (npairs - 1) + ((lane >> 3) & 1)] = tot;
+        red.step(1, hi8);
+        red.step(2, hi8);
+        red.step(3, hi8);
+        red.step(4, hi8);
+        const float tot = red.end();
+        if (writer) col[cbase + 2 * (npairs - 1)] = tot;
     }
 }
 
@@ -652,59 +679,60 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
 }
 
 // y = diag u - (row side + column sides), each row summed in a fixed order:
-// its row-side parts in CTA order, then the column sides of tile pairs (I', R)
-// for I' = 0 .. R-1.  One block per row tile R.
+// its row-side parts in CTA order, then the column sides of the tile pairs
+// (I', R), I' = 0 .. R-1.  Block (R, c) finishes rows R B + 64 c .. + 63 of
+// row tile R: its four groups of 64 threads sum the column sides of I' = g,
+// g + 4, g + 8, ... (g the group), and group 0 adds the four group sums in
+// order of g.
+constexpr int kSymFinRows = 64;
+constexpr int kSymFinThreads = 256;
+
 template <int T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSymFinThreads)
 matvec_sym_finalize(const double *__restrict__ u, int64_t N, double diag1, double diag2, SymPlan plan,
                     const double *__restrict__ islots, const double *__restrict__ iside,
                     const float *__restrict__ jpart, double *__restrict__ y, const int *__restrict__ skip) {
-    constexpr int B = kF32Threads * T;
+    constexpr int B = kF32Threads * T, NG = kSymFinThreads / kSymFinRows;
+    static_assert(B % kSymFinRows == 0, "row chunks");
     if (skip != nullptr && *((volatile const int *)skip)) return;
+    __shared__ double s_part[NG][2][kSymFinRows];
     const int64_t Tt = plan.tiles;
     const int64_t R = blockIdx.x;
+    const int g = threadIdx.x / kSymFinRows;
+    const int k = blockIdx.y * kSymFinRows + (threadIdx.x % kSymFinRows);
+    double a1 = 0.0, a2 = 0.0;
+    for (int64_t Ip = g; Ip < R; Ip += NG) {
+        const float *jp = jpart + sym_offdiag_index(Ip, R, Tt) * 2 * B;
+        a1 += (double)jp[k];
+        a2 += (double)jp[B + k];
+    }
+    s_part[g][0][threadIdx.x % kSymFinRows] = a1;
+    s_part[g][1][threadIdx.x % kSymFinRows] = a2;
+    __syncthreads();
+    if (g != 0) return;
+    const int64_t i = R * B + k;
+    if (i >= N) return;
     const int64_t c0 = sk_cta_of(sym_row_start(R, Tt), plan.work, plan.ctas);
     const int64_t c1 = sk_cta_of(sym_row_start(R + 1, Tt) - 1, plan.work, plan.ctas);
-    for (int k = threadIdx.x; k < B; k += blockDim.x) {
-        const int64_t i = R * B + k;
-        if (i >= N) break;
-        double s1 = 0.0, s2 = 0.0;
-        if (c0 == c1) {
-            s1 = iside[R * 2 * B + k];
-            s2 = iside[R * 2 * B + B + k];
-        } else {
-            for (int64_t cc = c0; cc <= c1; ++cc) {
-                const int64_t first = sym_row_of(sk_begin(cc, plan.work, plan.ctas), Tt);
-                const double *sl = islots + (2 * cc + (R == first ? 0 : 1)) * 2 * B;
-                s1 += sl[k];
-                s2 += sl[B + k];
-            }
+    double s1 = 0.0, s2 = 0.0;
+    if (c0 == c1) {
+        s1 = iside[R * 2 * B + k];
+        s2 = iside[R * 2 * B + B + k];
+    } else {
+        for (int64_t cc = c0; cc <= c1; ++cc) {
+            const int64_t first = sym_row_of(sk_begin(cc, plan.work, plan.ctas), Tt);
+            const double *sl = islots + (2 * cc + (R == first ? 0 : 1)) * 2 * B;
+            s1 += sl[k];
+            s2 += sl[B + k];
         }
-        // column sides: four interleaved partial sums (I' mod 4), added in a
-        // fixed order, so that the loads and FP64 adds overlap
-        double a1[4] = {0.0, 0.0, 0.0, 0.0}, a2[4] = {0.0, 0.0, 0.0, 0.0};
-        int64_t Ip = 0;
-        for (; Ip + 4 <= R; Ip += 4) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const float *jp = jpart + sym_offdiag_index(Ip + v, R, Tt) * 2 * B;
-                a1[v] += (double)jp[k];
-                a2[v] += (double)jp[B + k];
-            }
-        }
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            if (Ip + v < R) {
-                const float *jp = jpart + sym_offdiag_index(Ip + v, R, Tt) * 2 * B;
-                a1[v] += (double)jp[k];
-                a2[v] += (double)jp[B + k];
-            }
-        }
-        s1 += (a1[0] + a1[1]) + (a1[2] + a1[3]);
-        s2 += (a2[0] + a2[1]) + (a2[2] + a2[3]);
-        y[i] = diag1 * u[i] - s1;
-        y[N + i] = diag2 * u[N + i] - s2;
     }
+#pragma unroll
+    for (int gg = 0; gg < NG; ++gg) {
+        s1 += s_part[gg][0][threadIdx.x];
+        s2 += s_part[gg][1][threadIdx.x];
+    }
+    y[i] = diag1 * u[i] - s1;
+    y[N + i] = diag2 * u[N + i] - s2;
 }
 
 // ---------------------------------------------------------------------------
@@ -837,8 +865,8 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         else                                                                                                    \
             matvec_sym_kernel<T, false, MINB><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(              \
                 ctx->pos32, ctx->nrm32, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);    \
-        matvec_sym_finalize<T><<<(unsigned)sp.tiles, 256, 0, ctx->stream>>>(u, ctx->N, diag1, diag2, sp,        \
-                                                                           islots, iside, jpart, y, skip_flag); \
+        matvec_sym_finalize<T><<<dim3((unsigned)sp.tiles, B / kSymFinRows), kSymFinThreads, 0, ctx->stream>>>(  \
+            u, ctx->N, diag1, diag2, sp, islots, iside, jpart, y, skip_flag);                                   \
         PB_LAUNCHED();                                                                                          \
     } while (0)
         switch (ctx->f32_variant) {
@@ -851,7 +879,6 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
             case MV_F32_PACKED_T3: PB_LAUNCH_F32X2(3); break;
             case MV_F32_SYM_T2: PB_LAUNCH_SYM(2, 4); break;
             case MV_F32_SYM_T4: PB_LAUNCH_SYM(4, 3); break;
-            case MV_F32_SYM_T4_O4: PB_LAUNCH_SYM(4, 4); break;
             default: PB_LAUNCH_F32X2(2); break;
         }
 #undef PB_LAUNCH_F32X2
@@ -901,9 +928,6 @@ int matvec_f32_occupancy(int variant) {
             break;
         case MV_F32_SYM_T4:
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false, 3>, kF32Threads, 0);
-            break;
-        case MV_F32_SYM_T4_O4:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false, 4>, kF32Threads, 0);
             break;
         default:
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<2, false>, kF32Threads, 0);
