@@ -171,7 +171,7 @@ def oracle_rate(prob, seconds: float, seed: int = 0):
     rng = np.random.Generator(np.random.PCG64(seed))
     u = rng.normal(size=2 * prob.n)
     eps = prob.eps2 / prob.eps1
-    probe = min(prob.n, 32)
+    probe = min(prob.n, 512)   # enough rows to occupy every host thread
     t = time.perf_counter()
     oracle.matvec_rows(s, eps, prob.kappa, u, rng.choice(prob.n, probe, replace=False))
     dt = max(time.perf_counter() - t, 1e-6)

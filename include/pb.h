@@ -163,11 +163,15 @@ pb_status pb_profile_read(pb_ctx *ctx, double *matvec_ms, int64_t *timed_launche
  * a GMRES instance (Section 2.4, restarted, x0 = 0) solved with FP32-pair
  * products; all instances advance in lockstep and each lockstep product is one
  * persistent launch over all surfaces that evaluates K1..K4 once per pair for
- * all charge sets of a surface.  All work runs on ctxs[0]'s stream; the other
+ * all charge sets of a surface; a surface with a single charge set whose
+ * context is configured for a symmetric product variant (the default for
+ * N >= 16,384) takes its own launch of that product instead.  All work runs
+ * on ctxs[0]'s stream; the other
  * contexts must not be in use meanwhile.  use_graph = 1 captures one restart
  * cycle of the whole batch in a CUDA graph and replays it (ignored on the
  * legacy default stream); 0 launches the kernels one by one; 2 launches them
- * one by one and times every product launch with CUDA events (matvec_ms).  energies: host array of sum(nrhs) doubles (kcal/mol,
+ * one by one and times every product launch with CUDA events (matvec_ms).
+ * energies: host array of sum(nrhs) doubles (kcal/mol,
  * Eq. (14)), in surface-major order.  Returns PB_ERR_NOCONV if an instance
  * reached maxit (energies still filled).  This is a library extension for
  * throughput; the paper solves one molecule per run. */
