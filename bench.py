@@ -52,6 +52,8 @@ MATVEC_KERNELS = {
     4: ("matvec_f32x2_kernel<3>", 39, 18),
     5: ("matvec_sym_kernel<2> + matvec_sym_finalize<2>", 23, 10),
     6: ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", 23, 10),
+    7: ("matvec_sym_kernel<4, smem acc> + matvec_sym_finalize<4>", 23, 10),
+    8: ("matvec_sym_kernel<4, smem acc, 4 CTAs/SM> + matvec_sym_finalize<4>", 23, 10),
 }
 
 
@@ -62,7 +64,11 @@ def matvec_peak_gpairs(ops_per_pair):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel on
 # the 81,920-triangle sphere, from an ncu capture of the kernel as it is now
 # (profiles/); a kernel that changed since its capture has no entry.
-MATVEC_TRAFFIC_BYTES = {}
+MATVEC_TRAFFIC_BYTES = {
+    # profiles/matvec_sym_kernel_sphere2_full.md: both kernels of one product,
+    # ncu cold-cache replay (the finishing kernel's 58 MB come from L2 in a solve)
+    ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", "sphere2"): 3961600 + 1883648 + 58419456 + 47360,
+}
 
 WORKLOADS = {
     "sphere2": "Kirkwood sphere R=20 A, icosphere level 6 (81,920 triangles), 20 charges in 0.8R, "

@@ -101,6 +101,94 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+struct BConsts {
+    float2 nk2, mkap2, one2, mone2, three2, mthree2, meps2, epsm1, ieps2, omieps;
+};
+
+// K1..K4 of one target against one staged source pair (K0: only K2 and K3,
+// their constant factors being in the weights).
+template <bool K0>
+__device__ __forceinline__ void bcoef(const float4 &A, const float4 &Bq, const float4 &C, float2 x, float2 y,
+                                      float2 z, float2 nx, float2 ny, float2 nz, const BConsts &k, float2 &k1,
+                                      float2 &k2, float2 &k3, float2 &k4) {
+    const float2 dx = p_add(x, make_float2(A.x, A.y)), dy = p_add(y, make_float2(A.z, A.w));
+    const float2 dz = p_add(z, make_float2(Bq.x, Bq.y));
+    const float2 snx = make_float2(Bq.z, Bq.w), sny = make_float2(C.x, C.y), snz = make_float2(C.z, C.w);
+    const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
+    float2 inv, inv2;
+    inv.x = fminf(rsqrt_approx(r2.x), 1e9f);
+    inv.y = fminf(rsqrt_approx(r2.y), 1e9f);
+    if (K0) {
+        inv2 = p_mul(inv, inv);
+    } else {
+        inv2.x = fminf(rcp_approx(r2.x), 1e18f);
+        inv2.y = fminf(rcp_approx(r2.y), 1e18f);
+    }
+    const float2 inv3 = p_mul(inv2, inv);
+    const float2 ncx = p_fma(dx, nx, p_fma(dy, ny, p_mul(dz, nz)));   // -c_x
+    const float2 cy = p_fma(dx, snx, p_fma(dy, sny, p_mul(dz, snz)));
+    if (K0) {
+        k2 = p_mul(cy, inv3);
+        k3 = p_mul(ncx, inv3);
+    } else {
+        const float2 rho = p_mul(r2, inv);
+        const float2 arg = p_mul(k.nk2, rho);
+        float2 e;
+        e.x = exp2_approx(arg.x);
+        e.y = exp2_approx(arg.y);
+        const float2 mkr = p_mul(k.mkap2, rho);
+        const float2 nnn = p_fma(nx, snx, p_fma(ny, sny, p_mul(nz, snz)));   // -n
+        const float2 ome = p_fma(e, k.mone2, k.one2);
+        const float2 ome1 = p_fma(e, mkr, ome);                                // 1 - e (1 + kappa rho)
+        k1 = p_mul(ome, inv);
+        k2 = p_mul(p_mul(p_fma(ome1, k.meps2, k.epsm1), inv3), cy);
+        k3 = p_mul(p_mul(p_fma(ome1, k.ieps2, k.omieps), inv3), ncx);
+        const float2 p3 = p_fma(mkr, p_add(mkr, k.mthree2), k.three2);
+        const float2 e3 = p_fma(e, p3, k.mthree2);
+        const float2 ccy = p_mul(p_mul(e3, ncx), cy);
+        k4 = p_mul(p_fma(ccy, inv2, p_mul(ome1, nnn)), inv3);
+    }
+}
+
+// QU consecutive staged source pairs from q against the thread's T targets,
+// for the R right-hand sides of the surface.  With one target per thread two
+// pairs are taken at a time, so that two independent K1..K4 evaluations
+// overlap.
+template <int R, int T, int QU, bool K0>
+__device__ __forceinline__ void bstep(const float4 *s_g, const float4 *s_w, int q, const BConsts &k,
+                                      const float2 (&xi)[T], const float2 (&yi)[T], const float2 (&zi)[T],
+                                      const float2 (&nxi)[T], const float2 (&nyi)[T], const float2 (&nzi)[T],
+                                      float2 (&f1)[R][T], float2 (&f2)[R][T]) {
+    constexpr int TQ = kBSourceTile / 2;
+    float2 k1[QU][T], k2[QU][T], k3[QU][T], k4[QU][T];
+#pragma unroll
+    for (int v = 0; v < QU; ++v) {
+        const float4 A = s_g[q + v], Bq = s_g[TQ + q + v], C = s_g[2 * TQ + q + v];
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+            bcoef<K0>(A, Bq, C, xi[t], yi[t], zi[t], nxi[t], nyi[t], nzi[t], k, k1[v][t], k2[v][t], k3[v][t],
+                      k4[v][t]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int v = 0; v < QU; ++v) {
+            const float4 w = s_w[r * TQ + q + v];
+            const float2 wpsi = make_float2(w.x, w.y), wphi = make_float2(w.z, w.w);
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                if (K0) {
+                    f1[r][t] = p_fma(k2[v][t], wphi, f1[r][t]);
+                    f2[r][t] = p_fma(k3[v][t], wpsi, f2[r][t]);
+                } else {
+                    f1[r][t] = p_fma(k1[v][t], wpsi, p_fma(k2[v][t], wphi, f1[r][t]));
+                    f2[r][t] = p_fma(k3[v][t], wpsi, p_fma(k4[v][t], wphi, f2[r][t]));
+                }
+            }
+        }
+    }
+}
+
 // One staged tile of source pairs against the thread's T targets, for the R
 // right-hand sides of the surface.  Packed f32x2: each instruction does a
 // step of two pairs (one target, two sources).  The target normals arrive
@@ -119,67 +207,22 @@ __device__ __forceinline__ void bstage(const float4 *s_g, const float4 *s_w, int
                                        float kappa, float nk, const float2 (&xi)[T], const float2 (&yi)[T],
                                        const float2 (&zi)[T], const float2 (&nxi)[T], const float2 (&nyi)[T],
                                        const float2 (&nzi)[T], float2 (&f1)[R][T], float2 (&f2)[R][T]) {
-    constexpr int TQ = kBSourceTile / 2;
-    const float2 nk2 = p_dup(nk), mkap2 = p_dup(-kappa), one2 = p_dup(1.f), mone2 = p_dup(-1.f);
-    const float2 three2 = p_dup(3.f), mthree2 = p_dup(-3.f), meps2 = p_dup(-eps), epsm1 = p_dup(eps - 1.f);
-    const float2 ieps2 = p_dup(inv_eps), omieps = p_dup(1.f - inv_eps);
+    constexpr int QU = 1;     // two pairs per step at T = 1 measured slower (more registers)
+    BConsts k;
+    k.nk2 = p_dup(nk);
+    k.mkap2 = p_dup(-kappa);
+    k.one2 = p_dup(1.f);
+    k.mone2 = p_dup(-1.f);
+    k.three2 = p_dup(3.f);
+    k.mthree2 = p_dup(-3.f);
+    k.meps2 = p_dup(-eps);
+    k.epsm1 = p_dup(eps - 1.f);
+    k.ieps2 = p_dup(inv_eps);
+    k.omieps = p_dup(1.f - inv_eps);
+    int q = 0;
 #pragma unroll 1
-    for (int q = 0; q < npairs; ++q) {
-        const float4 A = s_g[q], Bq = s_g[TQ + q], C = s_g[2 * TQ + q];
-        const float2 mx = make_float2(A.x, A.y), my = make_float2(A.z, A.w), mz = make_float2(Bq.x, Bq.y);
-        const float2 snx = make_float2(Bq.z, Bq.w), sny = make_float2(C.x, C.y), snz = make_float2(C.z, C.w);
-        float4 w[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) w[r] = s_w[r * TQ + q];
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            const float2 dx = p_add(xi[t], mx), dy = p_add(yi[t], my), dz = p_add(zi[t], mz);
-            const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
-            float2 inv, inv2;
-            inv.x = fminf(rsqrt_approx(r2.x), 1e9f);
-            inv.y = fminf(rsqrt_approx(r2.y), 1e9f);
-            if (K0) {
-                inv2 = p_mul(inv, inv);
-            } else {
-                inv2.x = fminf(rcp_approx(r2.x), 1e18f);
-                inv2.y = fminf(rcp_approx(r2.y), 1e18f);
-            }
-            const float2 inv3 = p_mul(inv2, inv);
-            const float2 ncx = p_fma(dx, nxi[t], p_fma(dy, nyi[t], p_mul(dz, nzi[t])));   // -c_x
-            const float2 cy = p_fma(dx, snx, p_fma(dy, sny, p_mul(dz, snz)));
-            if (K0) {
-                const float2 k2 = p_mul(cy, inv3), k3 = p_mul(ncx, inv3);
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    f1[r][t] = p_fma(k2, make_float2(w[r].z, w[r].w), f1[r][t]);
-                    f2[r][t] = p_fma(k3, make_float2(w[r].x, w[r].y), f2[r][t]);
-                }
-            } else {
-                const float2 rho = p_mul(r2, inv);
-                const float2 arg = p_mul(nk2, rho);
-                float2 e;
-                e.x = exp2_approx(arg.x);
-                e.y = exp2_approx(arg.y);
-                const float2 mkr = p_mul(mkap2, rho);
-                const float2 nnn = p_fma(nxi[t], snx, p_fma(nyi[t], sny, p_mul(nzi[t], snz)));   // -n
-                const float2 ome = p_fma(e, mone2, one2);
-                const float2 ome1 = p_fma(e, mkr, ome);                                   // 1 - e (1 + kappa rho)
-                const float2 k1 = p_mul(ome, inv);
-                const float2 k2 = p_mul(p_mul(p_fma(ome1, meps2, epsm1), inv3), cy);
-                const float2 k3 = p_mul(p_mul(p_fma(ome1, ieps2, omieps), inv3), ncx);
-                const float2 p3 = p_fma(mkr, p_add(mkr, mthree2), three2);
-                const float2 e3 = p_fma(e, p3, mthree2);
-                const float2 ccy = p_mul(p_mul(e3, ncx), cy);
-                const float2 k4 = p_mul(p_fma(ccy, inv2, p_mul(ome1, nnn)), inv3);
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const float2 wpsi = make_float2(w[r].x, w[r].y), wphi = make_float2(w[r].z, w[r].w);
-                    f1[r][t] = p_fma(k1, wpsi, p_fma(k2, wphi, f1[r][t]));
-                    f2[r][t] = p_fma(k3, wpsi, p_fma(k4, wphi, f2[r][t]));
-                }
-            }
-        }
-    }
+    for (; q + QU <= npairs; q += QU) bstep<R, T, QU, K0>(s_g, s_w, q, k, xi, yi, zi, nxi, nyi, nzi, f1, f2);
+    if (QU > 1 && q < npairs) bstep<R, T, 1, K0>(s_g, s_w, q, k, xi, yi, zi, nxi, nyi, nzi, f1, f2);
 }
 
 // y_q = A u_q for every instance q; u_q = x_q (usel 0) or V_q[k] (usel 1), y_q = w_q.
@@ -1015,6 +1058,7 @@ pb_status Engine::cycle(bool use_graph, bool time_products) {
         }
         if (all && !mb->finished) {
             mb->finished = true;
+            dirty_ = true;        // the next cycle's work split covers the running surfaces only
         }
     }
     return PB_OK;

@@ -560,7 +560,9 @@ __device__ __forceinline__ void sym_stage(const float4 *s_a, const float4 *s_b, 
     }
 }
 
-template <int T, bool K0, int MINB>
+// SACC: the FP64 row-side sums live in shared memory (each thread its own
+// slots) instead of registers, which leaves registers for interleaving.
+template <int T, bool K0, int MINB, bool SACC>
 __global__ void __launch_bounds__(kF32Threads, MINB)
 matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm, const double *__restrict__ u,
                   int64_t N, F32Params prm, SymPlan plan, double *__restrict__ islots, double *__restrict__ iside,
@@ -572,6 +574,7 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
     __shared__ float4 s_a[TQ], s_b[TQ], s_c[TQ], s_d[TQ];
     __shared__ float s_col[NW][2][B];     // per-warp column sides of the current tile pair
+    __shared__ double s_acc[SACC ? 2 * T * BS : 1];
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t c = blockIdx.x;
@@ -610,9 +613,17 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
             wpi[t] = p_dup((float)u[N + i] * (w * wpsi_scale));
             wfi[t] = p_dup((float)u[i] * (w * wphi_scale));
         }
-        double acc1[T], acc2[T];
+        double acc1[SACC ? 1 : T], acc2[SACC ? 1 : T];
 #pragma unroll
-        for (int t = 0; t < T; ++t) { acc1[t] = 0.0; acc2[t] = 0.0; }
+        for (int t = 0; t < T; ++t) {
+            if constexpr (SACC) {
+                s_acc[t * BS + tid] = 0.0;
+                s_acc[(T + t) * BS + tid] = 0.0;
+            } else {
+                acc1[t] = 0.0;
+                acc2[t] = 0.0;
+            }
+        }
 
         for (; p < p_stop; ++p) {
             const int64_t J = I + (p - sym_row_start(I, Tt));
@@ -649,8 +660,13 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
                                            &s_col[warp][0][stg * TS], c3);
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
-                    acc1[t] += (double)f1[t].x + (double)f1[t].y;
-                    acc2[t] += (double)f2[t].x + (double)f2[t].y;
+                    if constexpr (SACC) {
+                        s_acc[t * BS + tid] += (double)f1[t].x + (double)f1[t].y;
+                        s_acc[(T + t) * BS + tid] += (double)f2[t].x + (double)f2[t].y;
+                    } else {
+                        acc1[t] += (double)f1[t].x + (double)f1[t].y;
+                        acc2[t] += (double)f2[t].x + (double)f2[t].y;
+                    }
                 }
             }
             if (!diag) {
@@ -672,8 +688,13 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
         double *dst = (c0 == c1) ? iside + I * 2 * B : islots + (2 * c + (I == I_first ? 0 : 1)) * 2 * B;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            dst[t * BS + tid] = acc1[t];
-            dst[B + t * BS + tid] = acc2[t];
+            if constexpr (SACC) {
+                dst[t * BS + tid] = s_acc[t * BS + tid];
+                dst[B + t * BS + tid] = s_acc[(T + t) * BS + tid];
+            } else {
+                dst[t * BS + tid] = acc1[t];
+                dst[B + t * BS + tid] = acc2[t];
+            }
         }
     }
 }
@@ -852,7 +873,7 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
                 ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,    \
                 ctx->mv_count);                                                                                 \
     } while (0)
-#define PB_LAUNCH_SYM(T, MINB)                                                                                      \
+#define PB_LAUNCH_SYM(T, MINB, SACC)                                                                                      \
     do {                                                                                                        \
         const SymPlan &sp = ctx->plansym;                                                                       \
         constexpr int B = kF32Threads * T;                                                                      \
@@ -860,10 +881,10 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         double *islots = iside + round256(sp.tiles * 2 * B * (int64_t)sizeof(double)) / sizeof(double);        \
         float *jpart = (float *)(islots + round256(sp.ctas * 4 * B * (int64_t)sizeof(double)) / sizeof(double)); \
         if (k0)                                                                                                 \
-            matvec_sym_kernel<T, true, MINB><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(               \
+            matvec_sym_kernel<T, true, MINB, SACC><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(               \
                 ctx->pos32, ctx->nrm32, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);    \
         else                                                                                                    \
-            matvec_sym_kernel<T, false, MINB><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(              \
+            matvec_sym_kernel<T, false, MINB, SACC><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(              \
                 ctx->pos32, ctx->nrm32, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);    \
         matvec_sym_finalize<T><<<dim3((unsigned)sp.tiles, B / kSymFinRows), kSymFinThreads, 0, ctx->stream>>>(  \
             u, ctx->N, diag1, diag2, sp, islots, iside, jpart, y, skip_flag);                                   \
@@ -877,8 +898,10 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
                 break;
             case MV_F32_PACKED_T4: PB_LAUNCH_F32X2(4); break;
             case MV_F32_PACKED_T3: PB_LAUNCH_F32X2(3); break;
-            case MV_F32_SYM_T2: PB_LAUNCH_SYM(2, 4); break;
-            case MV_F32_SYM_T4: PB_LAUNCH_SYM(4, 3); break;
+            case MV_F32_SYM_T2: PB_LAUNCH_SYM(2, 4, false); break;
+            case MV_F32_SYM_T4: PB_LAUNCH_SYM(4, 3, false); break;
+            case MV_F32_SYM_T4_SACC: PB_LAUNCH_SYM(4, 3, true); break;
+            case MV_F32_SYM_T4_SACC4: PB_LAUNCH_SYM(4, 4, true); break;
             default: PB_LAUNCH_F32X2(2); break;
         }
 #undef PB_LAUNCH_F32X2
@@ -924,10 +947,16 @@ int matvec_f32_occupancy(int variant) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<3, false>, kF32Threads, 0);
             break;
         case MV_F32_SYM_T2:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<2, false, 4>, kF32Threads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<2, false, 4, false>, kF32Threads, 0);
             break;
         case MV_F32_SYM_T4:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false, 3>, kF32Threads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false, 3, false>, kF32Threads, 0);
+            break;
+        case MV_F32_SYM_T4_SACC:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false, 3, true>, kF32Threads, 0);
+            break;
+        case MV_F32_SYM_T4_SACC4:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false, 4, true>, kF32Threads, 0);
             break;
         default:
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<2, false>, kF32Threads, 0);
