@@ -52,8 +52,6 @@ MATVEC_KERNELS = {
     4: ("matvec_f32x2_kernel<3>", 39, 18),
     5: ("matvec_sym_kernel<2> + matvec_sym_finalize<2>", 23, 10),
     6: ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", 23, 10),
-    7: ("matvec_sym_kernel<4, smem acc> + matvec_sym_finalize<4>", 23, 10),
-    8: ("matvec_sym_kernel<4, smem acc, 4 CTAs/SM> + matvec_sym_finalize<4>", 23, 10),
 }
 
 

@@ -116,13 +116,16 @@ __device__ __forceinline__ void bcoef(const float4 &A, const float4 &Bq, const f
     const float2 snx = make_float2(Bq.z, Bq.w), sny = make_float2(C.x, C.y), snz = make_float2(C.z, C.w);
     const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
     float2 inv, inv2;
-    inv.x = fminf(rsqrt_approx(r2.x), 1e9f);
-    inv.y = fminf(rsqrt_approx(r2.y), 1e9f);
+    // r^2 clamped below at 1e-18 for the MUFU; rho = r^2 (1/rho) uses the
+    // unclamped r^2, exactly 0 for a pair at zero distance
+    const float r2cx = fmaxf(r2.x, 1e-18f), r2cy = fmaxf(r2.y, 1e-18f);
+    inv.x = rsqrt_approx(r2cx);
+    inv.y = rsqrt_approx(r2cy);
     if (K0) {
         inv2 = p_mul(inv, inv);
     } else {
-        inv2.x = fminf(rcp_approx(r2.x), 1e18f);
-        inv2.y = fminf(rcp_approx(r2.y), 1e18f);
+        inv2.x = rcp_approx(r2cx);
+        inv2.y = rcp_approx(r2cy);
     }
     const float2 inv3 = p_mul(inv2, inv);
     const float2 ncx = p_fma(dx, nx, p_fma(dy, ny, p_mul(dz, nz)));   // -c_x
@@ -200,8 +203,8 @@ __device__ __forceinline__ void bstep(const float4 *s_g, const float4 *s_w, int 
 // 36 FP32 operations per pair for K1..K4 and 4 per right-hand side.  With
 // kappa = 0 (K0), K1 = K4 = 0 and the constant factors of K2, K3 are folded
 // into the staged weights: 16 operations per pair and 2 per right-hand side.
-// The self pair is removed by the clamps on 1/rho and 1/rho^2 (every term an
-// exact zero, as in the single-surface kernels).
+// The self pair is removed by the clamp of r^2 before the MUFU (every term
+// an exact zero, as in the single-surface kernels).
 template <int R, int T, bool K0>
 __device__ __forceinline__ void bstage(const float4 *s_g, const float4 *s_w, int npairs, float eps, float inv_eps,
                                        float kappa, float nk, const float2 (&xi)[T], const float2 (&yi)[T],

@@ -227,11 +227,12 @@ matvec_f32_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
 //   {-x0, -x1, -y0, -y1}  {-z0, -z1, nx0, nx1}  {ny0, ny1, nz0, nz1}  {Wdphi0, Wdphi1, Wphi0, Wphi1}
 // (W carries the 1/(4 pi)).  Each thread owns T targets, duplicated into both
 // halves of register pairs.  The singular self pair (and any pair at zero
-// distance) is removed by clamping 1/rho at 1e9 and 1/rho^2 at 1e18: then
-// rho = r2 * (1/rho) is exactly 0, exp2(0) is exactly 1, c_x = c_y = 0, and
+// distance) is removed by clamping r^2 from below at 1e-18 before the MUFU
+// rsqrt and rcp (so 1/rho <= 1e9, 1/rho^2 <= 1e18): rho = r2 * (1/rho) with
+// the unclamped r2 is exactly 0, exp2(0) is exactly 1, c_x = c_y = 0, and
 // every term of K1..K4 is an exact zero.  The weights times 1/rho^3 <= 1e27
 // stay finite for |W u| < 3e11, so no infinity is formed.  Real pairs have
-// 1/rho < 1e9 (rho > 1e-9 A).
+// rho > 1e-9 A, where the clamp does nothing.
 //
 // Per pair and kappa > 0 the FP32 pipe does 39 operations: r (3), rho^2 (3),
 // rho (1), the exp2 argument (1), kappa rho (1), e (1 + kappa rho) (1),
@@ -254,8 +255,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-constexpr float kInvRhoMax = 1e9f;
-constexpr float kInvRho2Max = 1e18f;
+// r^2 is clamped from below before the MUFU rsqrt / rcp, so 1/rho <= 1e9 and
+// 1/rho^2 <= 1e18; rho = r^2 (1/rho) takes the unclamped r^2 and is exactly 0
+// for a pair at zero distance.
+constexpr float kRho2Min = 1e-18f;
 
 template <int T, bool K0>
 __global__ void __launch_bounds__(kF32Threads)
@@ -332,13 +335,14 @@ matvec_f32x2_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ n
                     const float2 dx = p_add(xi[t], mx), dy = p_add(yi[t], my), dz = p_add(zi[t], mz);
                     const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
                     float2 inv, inv2;
-                    inv.x = fminf(rsqrt_approx(r2.x), kInvRhoMax);
-                    inv.y = fminf(rsqrt_approx(r2.y), kInvRhoMax);
+                    const float r2cx = fmaxf(r2.x, kRho2Min), r2cy = fmaxf(r2.y, kRho2Min);
+                    inv.x = rsqrt_approx(r2cx);
+                    inv.y = rsqrt_approx(r2cy);
                     if (K0) {
                         inv2 = p_mul(inv, inv);                // MUFU is busier than the FP32 pipe here
                     } else {
-                        inv2.x = fminf(rcp_approx(r2.x), kInvRho2Max);
-                        inv2.y = fminf(rcp_approx(r2.y), kInvRho2Max);
+                        inv2.x = rcp_approx(r2cx);
+                        inv2.y = rcp_approx(r2cy);
                     }
                     const float2 inv3 = p_mul(inv2, inv);
                     const float2 cx = p_fma(dx, nxi[t], p_fma(dy, nyi[t], p_mul(dz, nzi[t])));
@@ -489,13 +493,14 @@ __device__ __forceinline__ void sym_stage(const float4 *s_a, const float4 *s_b, 
             const float2 dx = p_add(xi[t], mx), dy = p_add(yi[t], my), dz = p_add(zi[t], mz);
             const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
             float2 inv, inv2;
-            inv.x = fminf(rsqrt_approx(r2.x), kInvRhoMax);
-            inv.y = fminf(rsqrt_approx(r2.y), kInvRhoMax);
+            const float r2cx = fmaxf(r2.x, kRho2Min), r2cy = fmaxf(r2.y, kRho2Min);
+            inv.x = rsqrt_approx(r2cx);
+            inv.y = rsqrt_approx(r2cy);
             if (K0) {
                 inv2 = p_mul(inv, inv);
             } else {
-                inv2.x = fminf(rcp_approx(r2.x), kInvRho2Max);
-                inv2.y = fminf(rcp_approx(r2.y), kInvRho2Max);
+                inv2.x = rcp_approx(r2cx);
+                inv2.y = rcp_approx(r2cy);
             }
             const float2 inv3 = p_mul(inv2, inv);
             const float2 ncx = p_fma(dx, nxi[t], p_fma(dy, nyi[t], p_mul(dz, nzi[t])));   // -c_x
@@ -560,9 +565,7 @@ __device__ __forceinline__ void sym_stage(const float4 *s_a, const float4 *s_b, 
     }
 }
 
-// SACC: the FP64 row-side sums live in shared memory (each thread its own
-// slots) instead of registers, which leaves registers for interleaving.
-template <int T, bool K0, int MINB, bool SACC>
+template <int T, bool K0, int MINB>
 __global__ void __launch_bounds__(kF32Threads, MINB)
 matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm, const double *__restrict__ u,
                   int64_t N, F32Params prm, SymPlan plan, double *__restrict__ islots, double *__restrict__ iside,
@@ -574,7 +577,6 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
     __shared__ float4 s_a[TQ], s_b[TQ], s_c[TQ], s_d[TQ];
     __shared__ float s_col[NW][2][B];     // per-warp column sides of the current tile pair
-    __shared__ double s_acc[SACC ? 2 * T * BS : 1];
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t c = blockIdx.x;
@@ -613,17 +615,9 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
             wpi[t] = p_dup((float)u[N + i] * (w * wpsi_scale));
             wfi[t] = p_dup((float)u[i] * (w * wphi_scale));
         }
-        double acc1[SACC ? 1 : T], acc2[SACC ? 1 : T];
+        double acc1[T], acc2[T];
 #pragma unroll
-        for (int t = 0; t < T; ++t) {
-            if constexpr (SACC) {
-                s_acc[t * BS + tid] = 0.0;
-                s_acc[(T + t) * BS + tid] = 0.0;
-            } else {
-                acc1[t] = 0.0;
-                acc2[t] = 0.0;
-            }
-        }
+        for (int t = 0; t < T; ++t) { acc1[t] = 0.0; acc2[t] = 0.0; }
 
         for (; p < p_stop; ++p) {
             const int64_t J = I + (p - sym_row_start(I, Tt));
@@ -660,13 +654,8 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
                                            &s_col[warp][0][stg * TS], c3);
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
-                    if constexpr (SACC) {
-                        s_acc[t * BS + tid] += (double)f1[t].x + (double)f1[t].y;
-                        s_acc[(T + t) * BS + tid] += (double)f2[t].x + (double)f2[t].y;
-                    } else {
-                        acc1[t] += (double)f1[t].x + (double)f1[t].y;
-                        acc2[t] += (double)f2[t].x + (double)f2[t].y;
-                    }
+                    acc1[t] += (double)f1[t].x + (double)f1[t].y;
+                    acc2[t] += (double)f2[t].x + (double)f2[t].y;
                 }
             }
             if (!diag) {
@@ -688,13 +677,8 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
         double *dst = (c0 == c1) ? iside + I * 2 * B : islots + (2 * c + (I == I_first ? 0 : 1)) * 2 * B;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            if constexpr (SACC) {
-                dst[t * BS + tid] = s_acc[t * BS + tid];
-                dst[B + t * BS + tid] = s_acc[(T + t) * BS + tid];
-            } else {
-                dst[t * BS + tid] = acc1[t];
-                dst[B + t * BS + tid] = acc2[t];
-            }
+            dst[t * BS + tid] = acc1[t];
+            dst[B + t * BS + tid] = acc2[t];
         }
     }
 }
@@ -873,7 +857,7 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
                 ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,    \
                 ctx->mv_count);                                                                                 \
     } while (0)
-#define PB_LAUNCH_SYM(T, MINB, SACC)                                                                                      \
+#define PB_LAUNCH_SYM(T, MINB)                                                                                      \
     do {                                                                                                        \
         const SymPlan &sp = ctx->plansym;                                                                       \
         constexpr int B = kF32Threads * T;                                                                      \
@@ -881,10 +865,10 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         double *islots = iside + round256(sp.tiles * 2 * B * (int64_t)sizeof(double)) / sizeof(double);        \
         float *jpart = (float *)(islots + round256(sp.ctas * 4 * B * (int64_t)sizeof(double)) / sizeof(double)); \
         if (k0)                                                                                                 \
-            matvec_sym_kernel<T, true, MINB, SACC><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(               \
+            matvec_sym_kernel<T, true, MINB><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(               \
                 ctx->pos32, ctx->nrm32, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);    \
         else                                                                                                    \
-            matvec_sym_kernel<T, false, MINB, SACC><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(              \
+            matvec_sym_kernel<T, false, MINB><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(              \
                 ctx->pos32, ctx->nrm32, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);    \
         matvec_sym_finalize<T><<<dim3((unsigned)sp.tiles, B / kSymFinRows), kSymFinThreads, 0, ctx->stream>>>(  \
             u, ctx->N, diag1, diag2, sp, islots, iside, jpart, y, skip_flag);                                   \
@@ -898,10 +882,8 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
                 break;
             case MV_F32_PACKED_T4: PB_LAUNCH_F32X2(4); break;
             case MV_F32_PACKED_T3: PB_LAUNCH_F32X2(3); break;
-            case MV_F32_SYM_T2: PB_LAUNCH_SYM(2, 4, false); break;
-            case MV_F32_SYM_T4: PB_LAUNCH_SYM(4, 3, false); break;
-            case MV_F32_SYM_T4_SACC: PB_LAUNCH_SYM(4, 3, true); break;
-            case MV_F32_SYM_T4_SACC4: PB_LAUNCH_SYM(4, 4, true); break;
+            case MV_F32_SYM_T2: PB_LAUNCH_SYM(2, 4); break;
+            case MV_F32_SYM_T4: PB_LAUNCH_SYM(4, 3); break;
             default: PB_LAUNCH_F32X2(2); break;
         }
 #undef PB_LAUNCH_F32X2
@@ -947,16 +929,10 @@ int matvec_f32_occupancy(int variant) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<3, false>, kF32Threads, 0);
             break;
         case MV_F32_SYM_T2:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<2, false, 4, false>, kF32Threads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<2, false, 4>, kF32Threads, 0);
             break;
         case MV_F32_SYM_T4:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false, 3, false>, kF32Threads, 0);
-            break;
-        case MV_F32_SYM_T4_SACC:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false, 3, true>, kF32Threads, 0);
-            break;
-        case MV_F32_SYM_T4_SACC4:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false, 4, true>, kF32Threads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_sym_kernel<4, false, 3>, kF32Threads, 0);
             break;
         default:
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_f32x2_kernel<2, false>, kF32Threads, 0);

@@ -39,16 +39,14 @@ enum MatvecVariant {
     MV_F32_PACKED_T4 = 3,
     MV_F32_PACKED_T3 = 4,
     MV_F32_SYM_T2 = 5,
-    MV_F32_SYM_T4 = 6,
-    MV_F32_SYM_T4_SACC = 7,    // as 6, FP64 row sums in shared memory
-    MV_F32_SYM_T4_SACC4 = 8    // as 7, built for 4 resident CTAs per SM
+    MV_F32_SYM_T4 = 6
 };
-constexpr int kNumF32Variants = 8;
+constexpr int kNumF32Variants = 6;
 __host__ __device__ constexpr int f32_variant_targets(int v) {
     return (v == MV_F32_PACKED_T2 || v == MV_F32_SYM_T2) ? 2 : (v == MV_F32_PACKED_T3 ? 3 : 4);
 }
 __host__ __device__ constexpr bool f32_variant_symmetric(int v) {
-    return v == MV_F32_SYM_T2 || v == MV_F32_SYM_T4 || v == MV_F32_SYM_T4_SACC || v == MV_F32_SYM_T4_SACC4;
+    return v == MV_F32_SYM_T2 || v == MV_F32_SYM_T4;
 }
 // FP64 kernel: 128 threads x 1 target, 128 sources per source tile.
 constexpr int kF64Threads = 128;
