@@ -57,6 +57,7 @@ def _lib():
         lib.oracle_energy.restype = ctypes.c_double
         lib.oracle_gauss.argtypes = [_I64, _D, _D, _D, _I64, _D, _D]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
         _LIB = lib
     return _LIB
 
@@ -71,6 +72,11 @@ def _f64(a) -> np.ndarray:
 
 def num_threads() -> int:
     return int(_lib().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops (a timing knob; results do not change)."""
+    _lib().oracle_set_num_threads(int(n))
 
 
 def _geom(surface):

@@ -215,3 +215,14 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the OpenMP loops above (timing only; results do not depend on it). */
+void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n < 1 ? 1 : n);
+#else
+    (void)n;
+#endif
+}
