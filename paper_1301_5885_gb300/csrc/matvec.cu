@@ -324,7 +324,7 @@ matvec_f32x2_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ n
             float2 f1[T], f2[T];
 #pragma unroll
             for (int t = 0; t < T; ++t) { f1[t] = p_dup(0.f); f2[t] = p_dup(0.f); }
-#pragma unroll 2
+#pragma unroll 4
             for (int q = 0; q < npairs; ++q) {
                 const float4 A = s_a[q], B = s_b[q], C = s_c[q], D = s_d[q];
                 const float2 mx = make_float2(A.x, A.y), my = make_float2(A.z, A.w), mz = make_float2(B.x, B.y);
@@ -482,7 +482,7 @@ __device__ __forceinline__ void sym_stage(const float4 *s_a, const float4 *s_b, 
     const int cbase = (lane >> 4) * B + ((lane >> 3) & 1);
     const bool writer = (lane & 7) == 0;
     WarpReduce4 red;
-#pragma unroll 2
+#pragma unroll 8
     for (int q = 0; q < npairs; ++q) {
         const float4 A = s_a[q], Bq = s_b[q], C = s_c[q], D = s_d[q];
         const float2 mx = make_float2(A.x, A.y), my = make_float2(A.z, A.w), mz = make_float2(Bq.x, Bq.y);
