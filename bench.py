@@ -65,7 +65,7 @@ def matvec_peak_gpairs(ops_per_pair):
 MATVEC_TRAFFIC_BYTES = {
     # profiles/matvec_sym_kernel_sphere2_full.md: both kernels of one product,
     # ncu cold-cache replay (the finishing kernel's 58 MB come from L2 in a solve)
-    ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", "sphere2"): 3961088 + 2006784 + 58419456 + 55808,
+    ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", "sphere2"): 4009472 + 1697536 + 58419712 + 25088,
 }
 
 WORKLOADS = {
