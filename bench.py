@@ -464,14 +464,19 @@ def run_matvec(args):
     stream = torch.cuda.current_stream()
     ctx = pb.pb_create(s.centroids, s.normals, s.areas, prob.charges, prob.eps1, prob.eps2, prob.kappa,
                        stream=stream)
-    if args.variant:
+    prec = args.prec
+    if prec == "fp64":
+        v64 = pb.pb_matvec_configure_fp64(ctx, args.variant)
+    elif args.variant:
         pb.pb_matvec_configure(ctx, args.variant, 0)
     cfg = pb.pb_matvec_get_config(ctx)
+    if prec == "fp64":
+        cfg["variant"] = v64
     gen = torch.Generator(device=dev).manual_seed(7)
     u = torch.randn(2 * prob.n, dtype=torch.float64, device=dev, generator=gen)
     y = torch.empty_like(u)
     for _ in range(args.warmup):
-        pb.pb_matvec(ctx, u, y, "fp32pair")
+        pb.pb_matvec(ctx, u, y, prec)
     torch.cuda.synchronize()
     sampler = _clock_and_uuid(torch, dev)
     sampler.start()
@@ -481,7 +486,7 @@ def run_matvec(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        pb.pb_matvec(ctx, u, y, "fp32pair")
+        pb.pb_matvec(ctx, u, y, prec)
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()
@@ -491,19 +496,27 @@ def run_matvec(args):
     ms = np.array([a.elapsed_time(b) for a, b in evs])
     pairs = prob.n * (prob.n - 1)
     value = pairs / (np.median(ms) * 1e-3) / 1e9
-    kname, ops_k, ops_0 = MATVEC_KERNELS[cfg["variant"]]
-    ops = ops_0 if prob.kappa == 0.0 else ops_k
-    peak = matvec_peak_gpairs(ops)
+    if prec == "fp64":
+        kname = {1: "matvec_f64_kernel", 2: "matvec_sym64_kernel<1> + finalize",
+                 3: "matvec_sym64_kernel<2> + finalize"}[cfg["variant"]]
+        peak = None
+    else:
+        kname, ops_k, ops_0 = MATVEC_KERNELS[cfg["variant"]]
+        ops = ops_0 if prob.kappa == 0.0 else ops_k
+        peak = matvec_peak_gpairs(ops)
     line = {"metric": "matvec Gpairs/s", "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.median(ms)), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs, f64 accumulation", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "f32 pairs, f64 accumulation", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_triangles": prob.n,
                        "variant": cfg["variant"], "ctas": cfg["ctas"],
                        "l2": "inputs L2-resident by design (the product is FP32-pipe bound)"},
             "roofline": {"kernel": kname, "bound": "alu", "achieved": value, "peak": peak, "unit": UNIT,
-                         "frac": value / peak, "traffic": MATVEC_TRAFFIC_BYTES.get((kname, args.workload)),
-                         "peak_basis": f"FP32 pipe: {SMS} SMs x 128 lanes x {SM_MAX_MHZ:.0f} MHz / {ops} FP32 ops "
-                                       "per ordered pair (derived)"},
+                         "frac": value / peak if peak else None,
+                         "traffic": MATVEC_TRAFFIC_BYTES.get((kname, args.workload)),
+                         "peak_basis": (f"FP32 pipe: {SMS} SMs x 128 lanes x {SM_MAX_MHZ:.0f} MHz / {ops} FP32 ops "
+                                        "per ordered pair (derived)") if peak else
+                                       "FP64 pipe (see the ncu FP64-pipe utilisation)"},
             "ms_min": float(ms.min()), "ms_max": float(ms.max()), "gpu_launches": launches, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0

@@ -265,6 +265,19 @@ pb_status pb_matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm);
 pb_status pb_matvec_get_config(pb_ctx *ctx, int *variant, int *ctas_per_sm, int64_t *ctas);
 pb_status pb_matvec_autotune(pb_ctx *ctx, int reps, int *variant, int *ctas_per_sm, double *best_ms);
 
+/* Kernel choice for the FP64 product (PB_FP64 in pb_matvec, and the residual
+ * of the refinement in pb_solve).  variant: 1 = plain (every ordered pair);
+ * 2 and 3 = symmetric with 1 and 2 targets per thread (each unordered pair of
+ * Eqs. (12)-(13) evaluated once for both rows, as in the FP32-pair variants
+ * 5 and 6, with FP64 column sides; scratch of about 8 N^2 / (128 t) bytes,
+ * t the targets per thread, allocated by the first product and freed when
+ * the plain variant is configured); 0 = the built-in default for the
+ * context's N (symmetric from N = 2,048, with 2 targets per thread from
+ * 65,536; pb_create applies it).  All variants do every pair and every sum in FP64; results
+ * differ only by summation order.  *variant_out (may be NULL) receives the
+ * variant now in use. */
+pb_status pb_matvec_configure_fp64(pb_ctx *ctx, int variant, int *variant_out);
+
 /* No-allocation matrix-vector product.  The paper has no counterpart: this is
  * a library convenience for callers that cannot call cudaMalloc (for example
  * code running under a framework whose caching allocator already owns all of

@@ -98,6 +98,7 @@ SIGNATURES = {
                             ctypes.POINTER(_Opts), _I, ctypes.POINTER(_D), ctypes.POINTER(_BatchInfo)]),
     "pb_matvec_get_config": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64)]),
     "pb_matvec_autotune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "pb_matvec_configure_fp64": (_I, [_VP, _I, ctypes.POINTER(_I)]),
 }
 
 _LIB = None
@@ -321,6 +322,14 @@ def pb_matvec_get_config(ctx: Context) -> dict:
     v, c, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
     _check(lib().pb_matvec_get_config(ctx.handle, ctypes.byref(v), ctypes.byref(c), ctypes.byref(g)), ctx)
     return {"variant": v.value, "ctas_per_sm": c.value, "ctas": g.value}
+
+
+def pb_matvec_configure_fp64(ctx: Context, variant: int = 0) -> int:
+    """FP64 product variant: 1 plain, 2/3 symmetric (1/2 targets per thread), 0 default.
+    Returns the variant in use."""
+    v = ctypes.c_int()
+    _check(lib().pb_matvec_configure_fp64(ctx.handle, int(variant), ctypes.byref(v)), ctx)
+    return v.value
 
 
 def pb_matvec_autotune(ctx: Context, reps: int = 3) -> dict:

@@ -56,6 +56,12 @@ namespace {
 int64_t round256(int64_t b) { return (b + 255) / 256 * 256; }
 }  // namespace
 
+int64_t sym64_scratch_bytes(const SymPlan &pl, int tile) {
+    return round256(pl.tiles * 2 * tile * (int64_t)sizeof(double)) +
+           round256(pl.ctas * 2 * 2 * tile * (int64_t)sizeof(double)) +
+           round256((pl.work - pl.tiles) * 2 * tile * (int64_t)sizeof(double));
+}
+
 int64_t sym_scratch_bytes(const SymPlan &pl, int tile) {
     return round256(pl.tiles * 2 * tile * (int64_t)sizeof(double)) +
            round256(pl.ctas * 2 * 2 * tile * (int64_t)sizeof(double)) +
@@ -693,12 +699,12 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
 constexpr int kSymFinRows = 64;
 constexpr int kSymFinThreads = 256;
 
-template <int T>
+template <int B, typename JT>
 __global__ void __launch_bounds__(kSymFinThreads)
 matvec_sym_finalize(const double *__restrict__ u, int64_t N, double diag1, double diag2, SymPlan plan,
                     const double *__restrict__ islots, const double *__restrict__ iside,
-                    const float *__restrict__ jpart, double *__restrict__ y, const int *__restrict__ skip) {
-    constexpr int B = kF32Threads * T, NG = kSymFinThreads / kSymFinRows;
+                    const JT *__restrict__ jpart, double *__restrict__ y, const int *__restrict__ skip) {
+    constexpr int NG = kSymFinThreads / kSymFinRows;
     static_assert(B % kSymFinRows == 0, "row chunks");
     if (skip != nullptr && *((volatile const int *)skip)) return;
     __shared__ double s_part[NG][2][kSymFinRows];
@@ -708,7 +714,7 @@ matvec_sym_finalize(const double *__restrict__ u, int64_t N, double diag1, doubl
     const int k = blockIdx.y * kSymFinRows + (threadIdx.x % kSymFinRows);
     double a1 = 0.0, a2 = 0.0;
     for (int64_t Ip = g; Ip < R; Ip += NG) {
-        const float *jp = jpart + sym_offdiag_index(Ip, R, Tt) * 2 * B;
+        const JT *jp = jpart + sym_offdiag_index(Ip, R, Tt) * 2 * B;
         a1 += (double)jp[k];
         a2 += (double)jp[B + k];
     }
@@ -818,13 +824,147 @@ matvec_f64_kernel(const double *__restrict__ g64, const double *__restrict__ u, 
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Symmetric FP64 product: the plain path's arithmetic (every pair and every
+// sum in FP64, the self pair and any pair at zero distance skipped), with each
+// unordered pair evaluated once for both rows as in the FP32-pair symmetric
+// kernel (same tiling, plan and finishing kernel; the column sides are kept in
+// FP64).  On GB300 the FP64 pipe bounds this path, so halving the pair
+// evaluations halves its time.  T targets per thread, B = 128 T, sources staged
+// 128 at a time; the column side of a source is reduced over the warp with a
+// reduce-scatter (xor 16, then 8, 4, 2, 1).
+// ---------------------------------------------------------------------------
+template <int T>
+__global__ void __launch_bounds__(kF64Threads)
+matvec_sym64_kernel(const double *__restrict__ g64, const double *__restrict__ u, int64_t N, F64Params prm,
+                    SymPlan plan, double *__restrict__ islots, double *__restrict__ iside,
+                    double *__restrict__ jpart, const int *__restrict__ skip,
+                    unsigned long long *__restrict__ evaluated) {
+    constexpr int BS = kF64Threads, B = BS * T, TS = BS, NW = BS / 32, STAGES = B / TS;
+    if (skip != nullptr && *((volatile const int *)skip)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
+    __shared__ double s_x[TS], s_y[TS], s_z[TS], s_nx[TS], s_ny[TS], s_nz[TS], s_wpsi[TS], s_wphi[TS];
+    __shared__ double s_col[NW][2][B];
+    const double *X = g64, *Y = g64 + N, *Z = g64 + 2 * N;
+    const double *NX = g64 + 3 * N, *NY = g64 + 4 * N, *NZ = g64 + 5 * N, *W = g64 + 6 * N;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool hi16 = (lane & 16) != 0;
+    const int64_t c = blockIdx.x;
+    const int64_t Tt = plan.tiles;
+    int64_t p = sk_begin(c, plan.work, plan.ctas);
+    const int64_t pend = sk_begin(c + 1, plan.work, plan.ctas);
+    const int64_t I_first = sym_row_of(p, Tt);
+
+    while (p < pend) {
+        const int64_t I = sym_row_of(p, Tt);
+        const int64_t row_end = sym_row_start(I + 1, Tt);
+        const int64_t p_stop = pend < row_end ? pend : row_end;
+        double xi[T], yi[T], zi[T], nxi[T], nyi[T], nzi[T], wpi[T], wfi[T], acc1[T], acc2[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int64_t i0 = I * B + t * BS + tid;
+            const int64_t i = i0 < N ? i0 : N - 1;
+            xi[t] = X[i]; yi[t] = Y[i]; zi[t] = Z[i];
+            nxi[t] = NX[i]; nyi[t] = NY[i]; nzi[t] = NZ[i];
+            const double w = i0 < N ? W[i] * kInv4Pi : 0.0;
+            wpi[t] = w * u[N + i];
+            wfi[t] = w * u[i];
+            acc1[t] = 0.0;
+            acc2[t] = 0.0;
+        }
+        for (; p < p_stop; ++p) {
+            const int64_t J = I + (p - sym_row_start(I, Tt));
+            const bool diag = (J == I);
+            for (int stg = 0; stg < STAGES; ++stg) {
+                const int64_t s0 = J * B + stg * TS;
+                if (s0 >= N) break;
+                __syncthreads();
+                {
+                    const int64_t j = s0 + tid;
+                    if (j < N) {
+                        const double w = W[j] * kInv4Pi;
+                        s_x[tid] = X[j]; s_y[tid] = Y[j]; s_z[tid] = Z[j];
+                        s_nx[tid] = NX[j]; s_ny[tid] = NY[j]; s_nz[tid] = NZ[j];
+                        s_wpsi[tid] = w * u[N + j];
+                        s_wphi[tid] = w * u[j];
+                    }
+                }
+                __syncthreads();
+                const int cnt = (int)((N - s0) < TS ? (N - s0) : TS);
+                for (int jj = 0; jj < cnt; ++jj) {
+                    double g1 = 0.0, g2 = 0.0;       // column side of source jj
+#pragma unroll
+                    for (int t = 0; t < T; ++t) {
+                        const double dx = xi[t] - s_x[jj], dy = yi[t] - s_y[jj], dz = zi[t] - s_z[jj];
+                        const double r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 > 0.0) {
+                            const double inv = rsqrt(r2);
+                            const double rho = r2 * inv;
+                            const double kr = prm.kappa * rho;
+                            const double e = exp(-kr);
+                            const double e1 = e * (1.0 + kr);
+                            const double inv2 = inv * inv;
+                            const double inv3 = inv2 * inv;
+                            const double cx = dx * nxi[t] + dy * nyi[t] + dz * nzi[t];
+                            const double cy = dx * s_nx[jj] + dy * s_ny[jj] + dz * s_nz[jj];
+                            const double nn = nxi[t] * s_nx[jj] + nyi[t] * s_ny[jj] + nzi[t] * s_nz[jj];
+                            const double k1 = (1.0 - e) * inv;
+                            const double a = (prm.eps * e1 - 1.0) * inv3;
+                            const double b = (e1 * prm.inv_eps - 1.0) * inv3;
+                            const double k4 =
+                                ((e1 - 1.0) * nn - (e * (3.0 + 3.0 * kr + kr * kr) - 3.0) * cx * cy * inv2) * inv3;
+                            acc1[t] += k1 * s_wpsi[jj] + a * cy * s_wphi[jj];
+                            acc2[t] += b * cx * s_wpsi[jj] + k4 * s_wphi[jj];
+                            if (!diag) {
+                                g1 += k1 * wpi[t] - a * cx * wfi[t];
+                                g2 += k4 * wfi[t] - b * cy * wpi[t];
+                            }
+                        }
+                    }
+                    if (!diag) {
+                        // lanes 0-15 end with the warp's sum of g1, 16-31 of g2
+                        double keep = hi16 ? g2 : g1;
+                        keep += __shfl_xor_sync(0xffffffffu, hi16 ? g1 : g2, 16);
+                        keep += __shfl_xor_sync(0xffffffffu, keep, 8);
+                        keep += __shfl_xor_sync(0xffffffffu, keep, 4);
+                        keep += __shfl_xor_sync(0xffffffffu, keep, 2);
+                        keep += __shfl_xor_sync(0xffffffffu, keep, 1);
+                        if ((lane & 15) == 0) s_col[warp][lane >> 4][stg * TS + jj] = keep;
+                    }
+                }
+            }
+            if (!diag) {
+                __syncthreads();
+                double *dst = jpart + sym_offdiag_index(I, J, Tt) * 2 * B;
+                for (int x = tid; x < 2 * B; x += BS) {
+                    const int r = x / B, k = x - r * B;
+                    double v = s_col[0][r][k];
+#pragma unroll
+                    for (int w2 = 1; w2 < NW; ++w2) v += s_col[w2][r][k];
+                    dst[x] = v;
+                }
+            }
+        }
+        const int64_t c0 = sk_cta_of(sym_row_start(I, Tt), plan.work, plan.ctas);
+        const int64_t c1 = sk_cta_of(row_end - 1, plan.work, plan.ctas);
+        double *dst = (c0 == c1) ? iside + I * 2 * B : islots + (2 * c + (I == I_first ? 0 : 1)) * 2 * B;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            dst[t * BS + tid] = acc1[t];
+            dst[B + t * BS + tid] = acc2[t];
+        }
+    }
+}
+
 }  // namespace
 
 pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision prec, const int *skip_flag) {
     const double diag1 = 0.5 * (1.0 + ctx->eps), diag2 = 0.5 * (1.0 + 1.0 / ctx->eps);
     if (prec != PB_FP32PAIR && prec != PB_FP64)
         return set_error(ctx, PB_ERR_ARG, "pb_matvec: unknown precision %d", (int)prec);
-    if (prec == PB_FP32PAIR) {
+    {
         // the symmetric variants' scratch, allocated by the first product that needs it
         pb_status s = matvec_prepare(ctx);
         if (s != PB_OK) return s;
@@ -871,7 +1011,8 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         else                                                                                                    \
             matvec_sym_kernel<T, false, MINB><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(              \
                 ctx->pos32, ctx->nrm32, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);    \
-        matvec_sym_finalize<T><<<dim3((unsigned)sp.tiles, B / kSymFinRows), kSymFinThreads, 0, ctx->stream>>>(  \
+        matvec_sym_finalize<B, float><<<dim3((unsigned)sp.tiles, B / kSymFinRows), kSymFinThreads, 0,          \
+                                        ctx->stream>>>(                                                         \
             u, ctx->N, diag1, diag2, sp, islots, iside, jpart, y, skip_flag);                                   \
         PB_LAUNCHED();                                                                                          \
     } while (0)
@@ -889,11 +1030,33 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         }
 #undef PB_LAUNCH_F32X2
 #undef PB_LAUNCH_SYM
-    } else {
+    } else if (ctx->f64_variant == MV_F64_PLAIN) {
         F64Params prm{ctx->eps, 1.0 / ctx->eps, ctx->kappa, diag1, diag2};
         const StreamKPlan &pl = ctx->plan64;
         matvec_f64_kernel<<<(unsigned)pl.ctas, kF64Threads, 0, ctx->stream>>>(
             ctx->g64, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag, ctx->mv_count);
+    } else {
+        F64Params prm{ctx->eps, 1.0 / ctx->eps, ctx->kappa, diag1, diag2};
+        const SymPlan &sp = ctx->plansym64;
+        const int T = ctx->f64_variant == MV_F64_SYM_T2 ? 2 : 1;
+        const int B = kF64Threads * T;
+        double *iside = (double *)ctx->sym64_scratch;
+        double *islots = iside + round256(sp.tiles * 2 * B * (int64_t)sizeof(double)) / sizeof(double);
+        double *jpart = islots + round256(sp.ctas * 4 * B * (int64_t)sizeof(double)) / sizeof(double);
+        if (T == 2) {
+            matvec_sym64_kernel<2><<<(unsigned)sp.ctas, kF64Threads, 0, ctx->stream>>>(
+                ctx->g64, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);
+            matvec_sym_finalize<2 * kF64Threads, double>
+                <<<dim3((unsigned)sp.tiles, 2 * kF64Threads / kSymFinRows), kSymFinThreads, 0, ctx->stream>>>(
+                    u, ctx->N, diag1, diag2, sp, islots, iside, jpart, y, skip_flag);
+        } else {
+            matvec_sym64_kernel<1><<<(unsigned)sp.ctas, kF64Threads, 0, ctx->stream>>>(
+                ctx->g64, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);
+            matvec_sym_finalize<kF64Threads, double>
+                <<<dim3((unsigned)sp.tiles, kF64Threads / kSymFinRows), kSymFinThreads, 0, ctx->stream>>>(
+                    u, ctx->N, diag1, diag2, sp, islots, iside, jpart, y, skip_flag);
+        }
+        PB_LAUNCHED();
     }
     PB_LAUNCHED();
     if (timed) {
@@ -952,17 +1115,51 @@ int64_t plan_partials(const StreamKPlan &pl, int target_tile) {
     return pl.target_tiles * pl.max_segments * 2 * target_tile;
 }
 
-pb_status matvec_prepare(pb_ctx *ctx) {
-    if (!f32_variant_symmetric(ctx->f32_variant)) return PB_OK;
-    const int64_t need = sym_scratch_bytes(ctx->plansym, kF32Threads * f32_variant_targets(ctx->f32_variant));
-    if (need <= ctx->sym_scratch_len) return PB_OK;
-    if (ctx->sym_scratch) ctx_free(ctx, ctx->sym_scratch);
-    ctx->device_bytes -= ctx->sym_scratch_len;
-    ctx->sym_scratch = nullptr;
-    ctx->sym_scratch_len = 0;
-    pb_status s = ctx_alloc(ctx, &ctx->sym_scratch, (size_t)need, "symmetric matvec scratch");
+namespace {
+pb_status ensure_scratch(pb_ctx *ctx, void **buf, int64_t *len, int64_t need, const char *what) {
+    if (need <= *len) return PB_OK;
+    if (*buf) ctx_free(ctx, *buf);
+    ctx->device_bytes -= *len;
+    *buf = nullptr;
+    *len = 0;
+    pb_status s = ctx_alloc(ctx, buf, (size_t)need, what);
     if (s != PB_OK) return s;
-    ctx->sym_scratch_len = need;
+    *len = need;
+    return PB_OK;
+}
+}  // namespace
+
+pb_status matvec_prepare(pb_ctx *ctx) {
+    pb_status s = PB_OK;
+    if (f32_variant_symmetric(ctx->f32_variant))
+        s = ensure_scratch(ctx, &ctx->sym_scratch, &ctx->sym_scratch_len,
+                           sym_scratch_bytes(ctx->plansym, kF32Threads * f32_variant_targets(ctx->f32_variant)),
+                           "symmetric matvec scratch");
+    if (s == PB_OK && ctx->f64_variant != MV_F64_PLAIN)
+        s = ensure_scratch(ctx, &ctx->sym64_scratch, &ctx->sym64_scratch_len,
+                           sym64_scratch_bytes(ctx->plansym64,
+                                               kF64Threads * (ctx->f64_variant == MV_F64_SYM_T2 ? 2 : 1)),
+                           "symmetric FP64 matvec scratch");
+    return s;
+}
+
+pb_status matvec_configure_fp64(pb_ctx *ctx, int variant) {
+    if (variant < 1 || variant > kNumF64Variants)
+        return set_error(ctx, PB_ERR_ARG, "FP64 matvec variant %d is not one of 1..%d", variant, kNumF64Variants);
+    if (variant != MV_F64_PLAIN) {
+        const int T = variant == MV_F64_SYM_T2 ? 2 : 1;
+        int occ = 0;
+        if (T == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, matvec_sym64_kernel<2>, kF64Threads, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, matvec_sym64_kernel<1>, kF64Threads, 0);
+        if (occ < 1) occ = 1;
+        ctx->plansym64 = make_sym_plan(ctx->N, kF64Threads * T, (int64_t)ctx->num_sms * occ);
+    } else if (ctx->sym64_scratch) {
+        ctx_free(ctx, ctx->sym64_scratch);
+        ctx->device_bytes -= ctx->sym64_scratch_len;
+        ctx->sym64_scratch = nullptr;
+        ctx->sym64_scratch_len = 0;
+    }
+    ctx->f64_variant = variant;
     return PB_OK;
 }
 

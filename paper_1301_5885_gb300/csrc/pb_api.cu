@@ -84,7 +84,7 @@ pb_status stage(pb_ctx *ctx, const double *src, int64_t n, double **dst, const c
 void free_all(pb_ctx *ctx) {
     void *bufs[] = {ctx->g64, ctx->pos32, ctx->nrm32, ctx->charges, ctx->b, ctx->x, ctx->partials,
                     ctx->tile_counters, ctx->red, ctx->red_counter, ctx->scalar, ctx->V, ctx->w, ctx->r,
-                    ctx->d, ctx->rres, ctx->st, ctx->sym_scratch};
+                    ctx->d, ctx->rres, ctx->st, ctx->sym_scratch, ctx->sym64_scratch};
     for (void *p : bufs) ctx_free(ctx, p);
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
@@ -275,6 +275,7 @@ pb_status pb_create(const double *centroids, const double *normals, const double
         if (e != cudaSuccess) s = cuda_error(ctx, e, "counter reset");
     }
     if (s == PB_OK && sym_default) s = matvec_configure(ctx, sym_default, sym_cps);
+    if (s == PB_OK) s = matvec_configure_fp64(ctx, default_f64_variant(N));
     if (s == PB_OK) s = stage(ctx, centroids, 3 * N, &c_dev, "centroid staging");
     if (s == PB_OK) s = stage(ctx, normals, 3 * N, &n_dev, "normal staging");
     if (s == PB_OK) s = stage(ctx, areas, N, &a_dev, "area staging");

@@ -48,6 +48,10 @@ __host__ __device__ constexpr int f32_variant_targets(int v) {
 __host__ __device__ constexpr bool f32_variant_symmetric(int v) {
     return v == MV_F32_SYM_T2 || v == MV_F32_SYM_T4;
 }
+// FP64 product variants: the plain stream-K kernel, or the symmetric one with
+// 1 or 2 targets per thread.
+enum Matvec64Variant { MV_F64_PLAIN = 1, MV_F64_SYM_T1 = 2, MV_F64_SYM_T2 = 3 };
+constexpr int kNumF64Variants = 3;
 // FP64 kernel: 128 threads x 1 target, 128 sources per source tile.
 constexpr int kF64Threads = 128;
 constexpr int kF64TargetTile = kF64Threads;
@@ -148,6 +152,11 @@ struct pb_ctx {
     pb::SymPlan plansym{};
     void *sym_scratch = nullptr;
     int64_t sym_scratch_len = 0;   // bytes
+    // FP64 product variant (Matvec64Variant) and the symmetric one's plan and scratch
+    int f64_variant = 1;
+    pb::SymPlan plansym64{};
+    void *sym64_scratch = nullptr;
+    int64_t sym64_scratch_len = 0;
     unsigned int *tile_counters = nullptr;
     int64_t counters_len = 0;
 
@@ -213,8 +222,14 @@ pb_status matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm);
 // allocates the scratch the configured FP32 variant needs (on ctx->stream), so
 // that later products allocate nothing (for example inside a stream capture)
 pb_status matvec_prepare(pb_ctx *ctx);
+// FP64 product variant (Matvec64Variant); the symmetric ones allocate their
+// scratch with their first product
+pb_status matvec_configure_fp64(pb_ctx *ctx, int variant);
+int64_t sym64_scratch_bytes(const SymPlan &pl, int tile);
 // tune.cu: the stored or built-in FP32 kernel choice for this context's size
 void default_f32_config(pb_ctx *ctx, int *variant, int *ctas_per_sm);
+// built-in FP64 product variant for n points
+int default_f64_variant(int64_t n);
 // device scratch of the built-in default product for n points (an estimate
 // for admission control; the symmetric variants' scratch, else 0)
 int64_t default_scratch_bytes(int64_t n, int num_sms);

@@ -25,6 +25,11 @@ namespace {
 // symmetric ones 400 and 241.
 constexpr int64_t kSymT4MinN = 40960;
 constexpr int64_t kSymT2MinN = 16384;
+// FP64 product: the symmetric kernel halves the FP64-pipe work; timed on
+// GB300 at N = 5,120: 4.8 (plain), 11.8 (symmetric, 1 target per thread) and
+// 9.2 Gpairs/s (2 targets); at N = 81,920: 8.2, 13.6 and 13.9.
+constexpr int64_t kSym64T1MinN = 2048;
+constexpr int64_t kSym64T2MinN = 65536;
 constexpr int kBuckets = 256;
 
 struct TuneEntry {
@@ -42,6 +47,10 @@ int bucket_of(int64_t n) {
 }
 
 }  // namespace
+
+int default_f64_variant(int64_t n) {
+    return n >= kSym64T2MinN ? MV_F64_SYM_T2 : (n >= kSym64T1MinN ? MV_F64_SYM_T1 : MV_F64_PLAIN);
+}
 
 int64_t default_scratch_bytes(int64_t n, int num_sms) {
     const int v = n >= kSymT4MinN ? MV_F32_SYM_T4 : (n >= kSymT2MinN ? MV_F32_SYM_T2 : 0);
@@ -84,6 +93,14 @@ pb_status pb_matvec_get_config(pb_ctx *ctx, int *variant, int *ctas_per_sm, int6
     if (ctas_per_sm) *ctas_per_sm = ctx->f32_ctas_per_sm;
     if (ctas) *ctas = f32_variant_symmetric(ctx->f32_variant) ? ctx->plansym.ctas : ctx->plan32.ctas;
     return PB_OK;
+}
+
+pb_status pb_matvec_configure_fp64(pb_ctx *ctx, int variant, int *variant_out) {
+    if (!ctx) return set_error(nullptr, PB_ERR_ARG, "pb_matvec_configure_fp64: NULL context");
+    if (variant == 0) variant = default_f64_variant(ctx->N);
+    pb_status s = matvec_configure_fp64(ctx, variant);
+    if (variant_out) *variant_out = ctx->f64_variant;
+    return s;
 }
 
 pb_status pb_matvec_autotune(pb_ctx *ctx, int reps, int *variant, int *ctas_per_sm, double *best_ms) {

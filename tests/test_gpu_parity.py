@@ -65,11 +65,16 @@ def _surfaces():
 SURFACES = _surfaces()
 
 
+F64_VARIANTS = [1, 2, 3]   # plain, symmetric T1, symmetric T2
+
+
 @pytest.mark.parametrize("name,surf", SURFACES, ids=[s[0] for s in SURFACES])
 @pytest.mark.parametrize("kappa", [0.1257, 0.0])
-def test_matvec_fp64_matches_oracle(name, surf, kappa):
+@pytest.mark.parametrize("variant", F64_VARIANTS)
+def test_matvec_fp64_matches_oracle(name, surf, kappa, variant):
     u = _u(surf.n, 1)
     with _ctx(surf, kappa=kappa) as ctx:
+        assert _pb().pb_matvec_configure_fp64(ctx, variant) == variant
         y = _gpu_matvec(ctx, u, "fp64")
     ref = oracle.matvec(surf, 80.0, kappa, u)
     assert np.all(np.isfinite(y))
@@ -130,6 +135,35 @@ def test_symmetric_matvec_rows_split_over_ctas(variant, ctas_per_sm, kappa):
     assert np.linalg.norm(y1 - y3) <= 2e-5 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("variant", [2, 3])
+def test_symmetric_fp64_matvec_rows_split_over_ctas(variant):
+    """FP64 symmetric product with more tile pairs than CTAs (rows split over
+    CTAs, ragged last tile): FP64 parity and a fixed summation order."""
+    surf = pi.icosphere(8.0, 5)
+    surf = surf.subset(np.arange(surf.n - 77))
+    u = _u(surf.n, 14)
+    pb = _pb()
+    with _ctx(surf) as ctx:
+        pb.pb_matvec_configure_fp64(ctx, variant)
+        y1 = _gpu_matvec(ctx, u, "fp64")
+        y2 = _gpu_matvec(ctx, u, "fp64")
+        pb.pb_matvec_configure_fp64(ctx, 1)
+        y3 = _gpu_matvec(ctx, u, "fp64")
+    ref = oracle.matvec(surf, 80.0, 0.1257, u)
+    assert np.array_equal(y1, y2)
+    assert np.linalg.norm(y1 - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert np.max(np.abs(y1 - ref)) <= 1e-9 * np.max(np.abs(ref))
+    assert np.linalg.norm(y1 - y3) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_fp64_configure_rejects_unknown_variants():
+    surf = pi.icosphere(2.0, 1)
+    pb = _pb()
+    with _ctx(surf) as ctx:
+        with pytest.raises(pb.PBError):
+            pb.pb_matvec_configure_fp64(ctx, 4)
+
+
 def test_autotune_picks_a_valid_variant_with_the_same_result():
     pb = _pb()
     surf = pi.icosphere(8.0, 5)
@@ -147,12 +181,22 @@ def test_autotune_picks_a_valid_variant_with_the_same_result():
             pb.pb_matvec_configure(ctx, 7, 0)
 
 
-@pytest.mark.parametrize("prec,variant", [("fp64", 0)] + [("fp32pair", v) for v in F32_VARIANTS])
+PREC_VARIANTS = [("fp64", v) for v in F64_VARIANTS] + [("fp32pair", v) for v in F32_VARIANTS]
+
+
+def _configure(ctx, prec, variant):
+    if prec == "fp64":
+        _pb().pb_matvec_configure_fp64(ctx, variant)
+    else:
+        _pb().pb_matvec_configure(ctx, variant, 0)
+
+
+@pytest.mark.parametrize("prec,variant", PREC_VARIANTS)
 def test_matvec_is_identity_without_jump_or_salt(prec, variant):
     surf = pi.icosphere(2.0, 3)
     u = _u(surf.n, 3)
     with _ctx(surf, eps1=2.0, eps2=2.0, kappa=0.0) as ctx:
-        _pb().pb_matvec_configure(ctx, variant, 0)
+        _configure(ctx, prec, variant)
         y = _gpu_matvec(ctx, u, prec)
     assert np.array_equal(y, u)
 
@@ -167,14 +211,14 @@ def test_single_element_has_only_the_diagonal(prec):
     assert y[1] == 0.5 * (1 + 1 / 80.0) * -1.3
 
 
-@pytest.mark.parametrize("prec,variant", [("fp64", 0)] + [("fp32pair", v) for v in F32_VARIANTS])
+@pytest.mark.parametrize("prec,variant", PREC_VARIANTS)
 def test_duplicate_centroids_are_dropped_like_the_self_term(prec, variant):
     base = pi.icosphere(2.0, 2)
     idx = np.concatenate([np.arange(base.n), [7, 7, 100]])
     surf = base.subset(idx)
     u = _u(surf.n, 4)
     with _ctx(surf) as ctx:
-        _pb().pb_matvec_configure(ctx, variant, 0)
+        _configure(ctx, prec, variant)
         y = _gpu_matvec(ctx, u, prec)
     ref = oracle.matvec(surf, 80.0, 0.1257, u)
     tol = 1e-10 if prec == "fp64" else 2e-5
