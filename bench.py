@@ -55,6 +55,10 @@ MATVEC_KERNELS = {
 }
 
 
+MATVEC64_KERNELS = {1: "matvec_f64_kernel", 2: "matvec_sym64_kernel<1> + matvec_sym_finalize<128, double>",
+                    3: "matvec_sym64_kernel<2> + matvec_sym_finalize<256, double>"}
+
+
 def matvec_peak_gpairs(ops_per_pair):
     return SMS * 128 * SM_MAX_MHZ * 1e6 / ops_per_pair / 1e9
 
@@ -268,12 +272,14 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    variant_seen = []
+    variant_seen, variant64_seen = [], []
 
     def step(c, nr, a, q, profile=False):
         ctx = pb.pb_create(c, nr, a, q, prob.eps1, prob.eps2, prob.kappa, stream=stream)
         try:
             variant_seen.append(pb.pb_matvec_get_config(ctx)["variant"])
+            if args.prec == "fp64" and not variant64_seen:
+                variant64_seen.append(pb.pb_matvec_configure_fp64(ctx, 0))   # the default, as created
             if profile:
                 pb.pb_profile_enable(ctx, True)
             info = pb.pb_solve(ctx, restart=args.restart, tol=args.tol, maxit=2000, prec=args.prec)
@@ -329,7 +335,7 @@ def run_ours(args):
     variant = variant_seen[-1]
 
     result = None
-    kname, ops = "matvec_f64_kernel", None
+    kname, ops = MATVEC64_KERNELS.get(variant64_seen[-1] if variant64_seen else 1), None
     if args.prec == "fp32pair":
         kname, ops_k, ops_0 = MATVEC_KERNELS[variant]
         ops = ops_0 if prob.kappa == 0.0 else ops_k
@@ -517,8 +523,7 @@ def run_matvec(args):
     pairs = prob.n * (prob.n - 1)
     value = pairs / (np.median(ms) * 1e-3) / 1e9
     if prec == "fp64":
-        kname = {1: "matvec_f64_kernel", 2: "matvec_sym64_kernel<1> + finalize",
-                 3: "matvec_sym64_kernel<2> + finalize"}[cfg["variant"]]
+        kname = MATVEC64_KERNELS[cfg["variant"]]
         peak = None
     else:
         kname, ops_k, ops_0 = MATVEC_KERNELS[cfg["variant"]]
