@@ -686,7 +686,7 @@ pb_status Engine::grow(void **p, size_t *cap, size_t need, size_t elem, const ch
     if (*p) cudaFreeAsync(*p, stream_);
     *p = nullptr;
     size_t n = need < 16 ? 16 : need + need / 2;
-    cudaError_t e = cudaMallocAsync(p, n * elem, stream_);
+    cudaError_t e = pool_alloc(p, n * elem, stream_);
     if (e != cudaSuccess) {
         *cap = 0;
         *p = nullptr;
@@ -714,9 +714,9 @@ EngineMember *Engine::add(pb_ctx *surf, const double *charges_host, int64_t nc, 
     mb->tag = tag;
     const int64_t n2 = 2 * surf->N;
     const size_t per = (size_t)(m_ + 5) * n2;
-    cudaError_t e = cudaMallocAsync((void **)&mb->vec, per * nrhs * sizeof(double), stream_);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&mb->st, nrhs * sizeof(GmresState), stream_);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&mb->q, (nc > 0 ? nc * nrhs : 1) * sizeof(Charge4), stream_);
+    cudaError_t e = pool_alloc((void **)&mb->vec, per * nrhs * sizeof(double), stream_);
+    if (e == cudaSuccess) e = pool_alloc((void **)&mb->st, nrhs * sizeof(GmresState), stream_);
+    if (e == cudaSuccess) e = pool_alloc((void **)&mb->q, (nc > 0 ? nc * nrhs : 1) * sizeof(Charge4), stream_);
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (mb->vec) cudaFreeAsync(mb->vec, stream_);
@@ -897,7 +897,7 @@ pb_status Engine::rebuild() {
     if (s == PB_OK) s = grow((void **)&red_, &cap_red_, (size_t)(m_ + 1) * nchunks_, sizeof(double), "engine reductions");
     if (s == PB_OK) s = grow((void **)&part_, &cap_part_, (size_t)2 * G_ * 2 * R_ * TT, sizeof(double), "engine partials");
     if (s == PB_OK && !scalar_) {
-        cudaError_t e = cudaMallocAsync((void **)&scalar_, 64 * sizeof(double), stream_);
+        cudaError_t e = pool_alloc((void **)&scalar_, 64 * sizeof(double), stream_);
         if (e != cudaSuccess) s = cuda_fail(e, "engine scalars");
     }
     if (s == PB_OK && cap_status_ < (size_t)nq_) {
@@ -1072,7 +1072,7 @@ pb_status Engine::energies(EngineMember *mb, double *out) {
     const int64_t n2 = 2 * c->N;
     const size_t per = (size_t)(m_ + 5) * n2;
     if (!scalar_) {
-        cudaError_t e = cudaMallocAsync((void **)&scalar_, 64 * sizeof(double), stream_);
+        cudaError_t e = pool_alloc((void **)&scalar_, 64 * sizeof(double), stream_);
         if (e != cudaSuccess) return cuda_fail(e, "engine scalars");
     }
     Charge4 *keep_q = c->charges;

@@ -167,17 +167,17 @@ pb_status gauss_check(pb_ctx *ctx, double *gmin, double *gmax) {
     PB_LAUNCHED();
     cudaError_t e = cudaGetLastError();
     double *h = nullptr;
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&h, ctx->Nc * sizeof(double));
+    if (e == cudaSuccess) e = pinned_alloc((void **)&h, ctx->Nc * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, out, ctx->Nc * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
-        if (h) cudaFreeHost(h);
+        pinned_free(h, ctx->Nc * sizeof(double));
         ctx_free(ctx, out);
         return cuda_error(ctx, e, "gauss check");
     }
     double lo = h[0], hi = h[0];
     for (int64_t k = 1; k < ctx->Nc; ++k) { lo = fmin(lo, h[k]); hi = fmax(hi, h[k]); }
-    cudaFreeHost(h);
+    pinned_free(h, ctx->Nc * sizeof(double));
     ctx_free(ctx, out);
     *gmin = lo;
     *gmax = hi;

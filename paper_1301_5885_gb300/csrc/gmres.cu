@@ -265,7 +265,7 @@ static pb_status ensure_workspace(pb_ctx *ctx, int m) {
     if (!ctx->r && (s = ctx_alloc(ctx, (void **)&ctx->r, n2 * sizeof(double), "gmres r")) != PB_OK) return s;
     if (!ctx->st && (s = ctx_alloc(ctx, (void **)&ctx->st, sizeof(GmresState), "gmres state")) != PB_OK) return s;
     if (!ctx->st_host) {
-        cudaError_t e = cudaMallocHost((void **)&ctx->st_host, sizeof(GmresState));
+        cudaError_t e = pinned_alloc((void **)&ctx->st_host, sizeof(GmresState));
         if (e != cudaSuccess) return cuda_error(ctx, e, "pinned gmres state");
     }
     return PB_OK;

@@ -7,6 +7,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+
 #include "pb_internal.cuh"
 
 namespace pb {
@@ -32,10 +35,77 @@ pb_status cuda_error(pb_ctx *ctx, cudaError_t e, const char *what) {
     return set_error(ctx, s, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
+// ---- memory: a library-owned stream-ordered pool per device, and a cache of
+// pinned host blocks.  The pool keeps freed memory (release threshold at its
+// maximum) so that contexts created and destroyed in a loop reuse it instead
+// of mapping it again; the pinned cache avoids a cudaMallocHost (and the
+// device synchronisation of cudaFreeHost) per context.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+static std::mutex g_pinned_mu;
+static std::multimap<size_t, void *> g_pinned;
+
+static size_t pinned_class(size_t bytes) {
+    size_t c = 256;
+    while (c < bytes) c <<= 1;
+    return c;
+}
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (dev >= 0 && dev < 64) {
+            if (!g_pool[dev]) {
+                cudaMemPoolProps props;
+                memset(&props, 0, sizeof(props));
+                props.allocType = cudaMemAllocationTypePinned;
+                props.handleTypes = cudaMemHandleTypeNone;
+                props.location.type = cudaMemLocationTypeDevice;
+                props.location.id = dev;
+                cudaMemPool_t created = nullptr;
+                if (cudaMemPoolCreate(&created, &props) == cudaSuccess) {
+                    uint64_t keep = UINT64_MAX;
+                    cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep);
+                    g_pool[dev] = created;
+                } else {
+                    cudaGetLastError();
+                }
+            }
+            pool = g_pool[dev];
+        }
+    }
+    if (pool) return cudaMallocFromPoolAsync(p, bytes, pool, stream);
+    return cudaMallocAsync(p, bytes, stream);
+}
+
+cudaError_t pinned_alloc(void **p, size_t bytes) {
+    const size_t c = pinned_class(bytes);
+    {
+        std::lock_guard<std::mutex> lock(g_pinned_mu);
+        auto it = g_pinned.find(c);
+        if (it != g_pinned.end()) {
+            *p = it->second;
+            g_pinned.erase(it);
+            return cudaSuccess;
+        }
+    }
+    return cudaMallocHost(p, c);
+}
+
+void pinned_free(void *p, size_t bytes) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    g_pinned.emplace(pinned_class(bytes), p);
+}
+
 pb_status ctx_alloc(pb_ctx *ctx, void **p, size_t bytes, const char *what) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+    cudaError_t e = pool_alloc(p, bytes, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -89,8 +159,8 @@ void free_all(pb_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
     ctx->prof_ev.clear();
-    if (ctx->host_scalar) cudaFreeHost(ctx->host_scalar);
-    if (ctx->st_host) cudaFreeHost(ctx->st_host);
+    pinned_free(ctx->host_scalar, 16 * sizeof(double));
+    pinned_free(ctx->st_host, sizeof(GmresState));
 }
 
 pb_status ensure_charge_capacity(pb_ctx *ctx, int64_t nc) {
@@ -264,7 +334,7 @@ pb_status pb_create(const double *centroids, const double *normals, const double
     if (s == PB_OK) s = ctx_alloc(ctx, (void **)&ctx->red_counter, 16 * sizeof(unsigned int), "reduction counters");
     if (s == PB_OK) s = ctx_alloc(ctx, (void **)&ctx->scalar, 16 * sizeof(double), "scalars");
     if (s == PB_OK) {
-        e = cudaMallocHost((void **)&ctx->host_scalar, 16 * sizeof(double));
+        e = pinned_alloc((void **)&ctx->host_scalar, 16 * sizeof(double));
         if (e != cudaSuccess) s = cuda_error(ctx, e, "pinned scalars");
     }
     if (s == PB_OK) {

@@ -201,6 +201,11 @@ void count_launch();
 void count_launches(int n);
 #define PB_LAUNCHED() ::pb::count_launch()
 
+// stream-ordered allocation from the library's pool of the current device
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t stream);
+// pinned host blocks, cached for reuse (pinned_free returns a block to the cache)
+cudaError_t pinned_alloc(void **p, size_t bytes);
+void pinned_free(void *p, size_t bytes);
 // allocation on the context's stream (stream-ordered pool)
 pb_status ctx_alloc(pb_ctx *ctx, void **p, size_t bytes, const char *what);
 void ctx_free(pb_ctx *ctx, void *p);

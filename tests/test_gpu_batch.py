@@ -79,6 +79,27 @@ def test_batched_energies_meet_the_bound_against_the_oracle():
         assert energies[0][r] == pytest.approx(ref, rel=1e-5)
 
 
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_of_only_direct_surfaces(use_graph):
+    """Every surface has one charge set on a symmetric-product context, so the
+    batched work list is empty and each surface takes its own product."""
+    pb = _pb()
+    probs = [pi.kirkwood_sphere_multi(level=5, radius=12.0 + 2 * k, n_charges=6, seed=70 + k,
+                                      kappa=(0.0 if k else 0.1257)) for k in range(2)]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctxs = [pb.pb_create(p.surface.centroids, p.surface.normals, p.surface.areas, p.charges, p.eps1, p.eps2,
+                             p.kappa, stream=stream) for p in probs]
+        energies, info = pb.pb_batch_solve(ctxs, [[p.charges] for p in probs], tol=1e-7, maxit=2000,
+                                           use_graph=use_graph)
+        assert info["converged"] == 2 and info["ctas"] == 0
+        for p, ctx, es in zip(probs, ctxs, energies):
+            single = pb.pb_solve(ctx, tol=1e-7, maxit=2000, prec="fp32pair").energy_kcal
+            assert es[0] == pytest.approx(single, rel=2e-6)
+        for c in ctxs:
+            pb.pb_destroy(c)
+
+
 def test_batch_rejects_bad_arguments():
     pb = _pb()
     p = pi.kirkwood_sphere_multi(level=2, radius=3.0, n_charges=2, seed=1)
