@@ -35,7 +35,7 @@ constexpr int kBThreads = 128;          // product kernel threads
 constexpr int kBSourceTile = 256;       // sources per staged tile (one pair per thread)
 // targets per thread of the product kernel for R right-hand sides (more
 // targets share each staged source when fewer accumulators are needed)
-__host__ __device__ constexpr int bmatvec_targets(int R) { return R <= 1 ? 4 : (R <= 4 ? 2 : 1); }
+__host__ __device__ constexpr int bmatvec_targets(int R) { return R <= 1 ? 4 : 2; }
 constexpr int kChunk = 4096;            // vector chunk (elements) of the GMRES kernels
 constexpr int kVThreads = 256;
 constexpr int LDH = kMaxRestart + 1;
@@ -153,40 +153,31 @@ __device__ __forceinline__ void bcoef(const float4 &A, const float4 &Bq, const f
     }
 }
 
-// QU consecutive staged source pairs from q against the thread's T targets,
-// for the R right-hand sides of the surface.  With one target per thread two
-// pairs are taken at a time, so that two independent K1..K4 evaluations
-// overlap.
-template <int R, int T, int QU, bool K0>
+// One staged source pair q against the thread's T targets, for the R
+// right-hand sides of the surface.
+template <int R, int T, bool K0>
 __device__ __forceinline__ void bstep(const float4 *s_g, const float4 *s_w, int q, const BConsts &k,
                                       const float2 (&xi)[T], const float2 (&yi)[T], const float2 (&zi)[T],
                                       const float2 (&nxi)[T], const float2 (&nyi)[T], const float2 (&nzi)[T],
                                       float2 (&f1)[R][T], float2 (&f2)[R][T]) {
     constexpr int TQ = kBSourceTile / 2;
-    float2 k1[QU][T], k2[QU][T], k3[QU][T], k4[QU][T];
+    float2 k1[T], k2[T], k3[T], k4[T];
+    const float4 A = s_g[q], Bq = s_g[TQ + q], C = s_g[2 * TQ + q];
 #pragma unroll
-    for (int v = 0; v < QU; ++v) {
-        const float4 A = s_g[q + v], Bq = s_g[TQ + q + v], C = s_g[2 * TQ + q + v];
-#pragma unroll
-        for (int t = 0; t < T; ++t)
-            bcoef<K0>(A, Bq, C, xi[t], yi[t], zi[t], nxi[t], nyi[t], nzi[t], k, k1[v][t], k2[v][t], k3[v][t],
-                      k4[v][t]);
-    }
+    for (int t = 0; t < T; ++t)
+        bcoef<K0>(A, Bq, C, xi[t], yi[t], zi[t], nxi[t], nyi[t], nzi[t], k, k1[t], k2[t], k3[t], k4[t]);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+        const float4 w = s_w[r * TQ + q];
+        const float2 wpsi = make_float2(w.x, w.y), wphi = make_float2(w.z, w.w);
 #pragma unroll
-        for (int v = 0; v < QU; ++v) {
-            const float4 w = s_w[r * TQ + q + v];
-            const float2 wpsi = make_float2(w.x, w.y), wphi = make_float2(w.z, w.w);
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                if (K0) {
-                    f1[r][t] = p_fma(k2[v][t], wphi, f1[r][t]);
-                    f2[r][t] = p_fma(k3[v][t], wpsi, f2[r][t]);
-                } else {
-                    f1[r][t] = p_fma(k1[v][t], wpsi, p_fma(k2[v][t], wphi, f1[r][t]));
-                    f2[r][t] = p_fma(k3[v][t], wpsi, p_fma(k4[v][t], wphi, f2[r][t]));
-                }
+        for (int t = 0; t < T; ++t) {
+            if (K0) {
+                f1[r][t] = p_fma(k2[t], wphi, f1[r][t]);
+                f2[r][t] = p_fma(k3[t], wpsi, f2[r][t]);
+            } else {
+                f1[r][t] = p_fma(k1[t], wpsi, p_fma(k2[t], wphi, f1[r][t]));
+                f2[r][t] = p_fma(k3[t], wpsi, p_fma(k4[t], wphi, f2[r][t]));
             }
         }
     }
@@ -210,7 +201,6 @@ __device__ __forceinline__ void bstage(const float4 *s_g, const float4 *s_w, int
                                        float kappa, float nk, const float2 (&xi)[T], const float2 (&yi)[T],
                                        const float2 (&zi)[T], const float2 (&nxi)[T], const float2 (&nyi)[T],
                                        const float2 (&nzi)[T], float2 (&f1)[R][T], float2 (&f2)[R][T]) {
-    constexpr int QU = 1;     // two pairs per step at T = 1 measured slower (more registers)
     BConsts k;
     k.nk2 = p_dup(nk);
     k.mkap2 = p_dup(-kappa);
@@ -222,10 +212,8 @@ __device__ __forceinline__ void bstage(const float4 *s_g, const float4 *s_w, int
     k.epsm1 = p_dup(eps - 1.f);
     k.ieps2 = p_dup(inv_eps);
     k.omieps = p_dup(1.f - inv_eps);
-    int q = 0;
 #pragma unroll 1
-    for (; q + QU <= npairs; q += QU) bstep<R, T, QU, K0>(s_g, s_w, q, k, xi, yi, zi, nxi, nyi, nzi, f1, f2);
-    if (QU > 1 && q < npairs) bstep<R, T, 1, K0>(s_g, s_w, q, k, xi, yi, zi, nxi, nyi, nzi, f1, f2);
+    for (int q = 0; q < npairs; ++q) bstep<R, T, K0>(s_g, s_w, q, k, xi, yi, zi, nxi, nyi, nzi, f1, f2);
 }
 
 // y_q = A u_q for every instance q; u_q = x_q (usel 0) or V_q[k] (usel 1), y_q = w_q.
@@ -245,6 +233,12 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
     __shared__ double *s_y[R];
     __shared__ int s_last;
     const int tid = threadIdx.x;
+    // FP64 row sums (rows of phi: w = 0, of dphi: w = 1): in registers, or in
+    // this thread's own shared-memory slots when there are many of them
+    constexpr bool SACC = R * T >= 16;
+    __shared__ double s_acc[SACC ? 2 * R * T * BS : 1];
+    double racc[SACC ? 1 : 2 * R * T];
+#define ACC(w, r, t) (SACC ? s_acc[(((w) * R + (r)) * T + (t)) * BS + tid] : racc[((w) * R + (r)) * T + (t)])
     const int64_t c = blockIdx.x;
     int64_t p = sk_begin(c, W, G);
     const int64_t pend = sk_begin(c + 1, W, G);
@@ -292,11 +286,10 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
             xi[t] = p_dup(q.x); yi[t] = p_dup(q.y); zi[t] = p_dup(q.z);
             nxi[t] = p_dup(-n.x); nyi[t] = p_dup(-n.y); nzi[t] = p_dup(-n.z);
         }
-        double acc1[R][T], acc2[R][T];
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int t = 0; t < T; ++t) { acc1[r][t] = 0.0; acc2[r][t] = 0.0; }
+            for (int t = 0; t < T; ++t) { ACC(0, r, t) = 0.0; ACC(1, r, t) = 0.0; }
 
         for (int64_t st = s_first; st < s_end; ++st) {
             __syncthreads();
@@ -341,8 +334,8 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
             for (int r = 0; r < R; ++r)
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
-                    acc1[r][t] += (double)f1[r][t].x + (double)f1[r][t].y;
-                    acc2[r][t] += (double)f2[r][t].x + (double)f2[r][t].y;
+                    ACC(0, r, t) += (double)f1[r][t].x + (double)f1[r][t].y;
+                    ACC(1, r, t) += (double)f2[r][t].x + (double)f2[r][t].y;
                 }
         }
 
@@ -358,8 +351,8 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         if (s_y[r]) {
-                            s_y[r][i] = sf.diag1 * s_u[r][i] - acc1[r][t];
-                            s_y[r][N + i] = sf.diag2 * s_u[r][N + i] - acc2[r][t];
+                            s_y[r][i] = sf.diag1 * s_u[r][i] - ACC(0, r, t);
+                            s_y[r][N + i] = sf.diag2 * s_u[r][N + i] - ACC(1, r, t);
                         }
                     }
                 }
@@ -371,8 +364,8 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
             for (int r = 0; r < R; ++r)
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
-                    mine[(2 * r) * TT + t * BS + tid] = acc1[r][t];
-                    mine[(2 * r + 1) * TT + t * BS + tid] = acc2[r][t];
+                    mine[(2 * r) * TT + t * BS + tid] = ACC(0, r, t);
+                    mine[(2 * r + 1) * TT + t * BS + tid] = ACC(1, r, t);
                 }
             __threadfence();
             __syncthreads();
@@ -414,6 +407,8 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
         p += s_end - s_first;
     }
 }
+
+#undef ACC
 
 // ---- batched GMRES vector kernels (one block per chunk) ----------------------
 __global__ void __launch_bounds__(kVThreads)
