@@ -54,8 +54,16 @@ typedef enum {
 
 typedef enum {
     PB_FP64 = 0,          /* every pair in FP64, FP64 accumulation */
-    PB_FP32PAIR = 1       /* pair arithmetic in FP32 (hardware rsqrt/exp2),
+    PB_FP32PAIR = 1,      /* pair arithmetic in FP32 (hardware rsqrt/exp2),
                              FP32 partial sums per source tile, FP64 row sums */
+    PB_FLOAT2 = 2         /* pair arithmetic in float-float (each value the
+                             unevaluated sum of two FP32 numbers, about 44
+                             bits; about 1e-12 relative per pair term) on the
+                             FP32 pipe, FP64 row sums: FP64-level products at
+                             several times the FP64 kernel's speed where the
+                             FP64 rate is a small fraction of FP32.  Accepted
+                             by pb_matvec and pb_solve (prec, refine_prec);
+                             pb_source and pb_energy_of reject it. */
 } pb_precision;
 
 typedef struct {
@@ -66,6 +74,9 @@ typedef struct {
     int refine;           /* number of FP64 iterative-refinement steps after a
                              PB_FP32PAIR solve: r = b - A_fp64 x, solve A d = r
                              with the same options, x += d.  0 = none */
+    pb_precision refine_prec; /* precision of the refinement residual product
+                             (and of the final residual check): PB_FP64 (the
+                             default, 0) or PB_FLOAT2 */
 } pb_solve_opts;
 
 typedef struct {

@@ -16,8 +16,9 @@ import numpy as np
 from . import build as _build
 
 PB_OK, PB_ERR_ARG, PB_ERR_BADMESH, PB_ERR_OOM, PB_ERR_CUDA, PB_ERR_NOCONV, PB_ERR_NAN, PB_ERR_TIMEOUT, PB_ERR_ADMIT = range(9)
-PB_FP64, PB_FP32PAIR = 0, 1
-PRECISIONS = {"fp64": PB_FP64, "fp32pair": PB_FP32PAIR, PB_FP64: PB_FP64, PB_FP32PAIR: PB_FP32PAIR}
+PB_FP64, PB_FP32PAIR, PB_FLOAT2 = 0, 1, 2
+PRECISIONS = {"fp64": PB_FP64, "fp32pair": PB_FP32PAIR, "float2": PB_FLOAT2,
+              PB_FP64: PB_FP64, PB_FP32PAIR: PB_FP32PAIR, PB_FLOAT2: PB_FLOAT2}
 
 
 class PBError(RuntimeError):
@@ -28,7 +29,7 @@ class PBError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
-                ("prec", ctypes.c_int), ("refine", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("refine", ctypes.c_int), ("refine_prec", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -254,8 +255,9 @@ def pb_matvec(ctx: Context, u, y, prec="fp32pair") -> None:
 
 
 def pb_solve(ctx: Context, restart: int = 10, tol: float = 1e-4, maxit: int = 1000, prec="fp32pair",
-             refine: int = 0, x0=None, x_out=None, raise_on_noconv: bool = True) -> SolveInfo:
-    o = _Opts(int(restart), float(tol), int(maxit), PRECISIONS[prec], int(refine))
+             refine: int = 0, x0=None, x_out=None, raise_on_noconv: bool = True,
+             refine_prec="fp64") -> SolveInfo:
+    o = _Opts(int(restart), float(tol), int(maxit), PRECISIONS[prec], int(refine), PRECISIONS[refine_prec])
     info = _Info()
     x0p = _device_vec(x0, 2 * ctx.n, "x0") if x0 is not None else None
     xop = _device_vec(x_out, 2 * ctx.n, "x_out") if x_out is not None else None
@@ -359,7 +361,7 @@ def pb_batch_solve(ctxs, charge_sets, restart: int = 10, tol: float = 1e-4, maxi
         ptrs[i] = a.ctypes.data if a.size else None
     total = sum(nr)
     en = (ctypes.c_double * total)()
-    o = _Opts(int(restart), float(tol), int(maxit), PB_FP32PAIR, 0)
+    o = _Opts(int(restart), float(tol), int(maxit), PB_FP32PAIR, 0, PB_FP64)
     info = _BatchInfo()
     mode = 2 if use_graph == "timed" else (1 if use_graph else 0)
     st = lib().pb_batch_solve(handles, n, ptrs, ncs, nr, ctypes.byref(o), mode, en, ctypes.byref(info))

@@ -1103,7 +1103,7 @@ extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double
         return set_error(nullptr, PB_ERR_ARG, "pb_batch_solve: NULL or empty argument");
     pb_ctx *lead = ctxs[0];
     if (!lead) return set_error(nullptr, PB_ERR_ARG, "pb_batch_solve: NULL context");
-    pb_solve_opts o{10, 1e-4, 1000, PB_FP32PAIR, 0};
+    pb_solve_opts o{10, 1e-4, 1000, PB_FP32PAIR, 0, PB_FP64};
     if (opts) {
         o = *opts;
         if (o.restart == 0) o.restart = 10;

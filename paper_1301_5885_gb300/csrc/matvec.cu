@@ -25,6 +25,7 @@
 #include <math.h>
 
 #include "fastmath.cuh"
+#include "finish.cuh"
 #include "pb_internal.cuh"
 
 namespace pb {
@@ -74,64 +75,6 @@ struct F32Params {
     float eps, inv_eps, kappa, neg_kappa_log2e;
     double diag1, diag2;
 };
-
-// Finish a segment: either write y directly (one CTA covers the whole target
-// tile) or publish partial rows and let the last arriving CTA reduce them.
-template <int TT, int T, int BS>
-__device__ __forceinline__ void finish_segment(const StreamKPlan &plan, int64_t a, int64_t c,
-                                               const double (&acc1)[T], const double (&acc2)[T],
-                                               const double *__restrict__ u, int64_t N, double diag1,
-                                               double diag2, double *__restrict__ partials,
-                                               unsigned int *__restrict__ counters, double *__restrict__ y) {
-    const int64_t S = plan.source_tiles;
-    const int64_t c0 = sk_cta_of(a * S, plan.work, plan.ctas);
-    const int64_t c1 = sk_cta_of(a * S + S - 1, plan.work, plan.ctas);
-    const int nseg = (int)(c1 - c0 + 1);
-    const int tid = threadIdx.x;
-    if (nseg == 1) {
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            int64_t i = a * TT + t * BS + tid;
-            if (i < N) {
-                y[i] = diag1 * u[i] - acc1[t];
-                y[N + i] = diag2 * u[N + i] - acc2[t];
-            }
-        }
-        return;
-    }
-    const int ord = (int)(c - c0);
-    double *mine = partials + ((a * plan.max_segments + ord) * 2) * TT;
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        mine[t * BS + tid] = acc1[t];
-        mine[TT + t * BS + tid] = acc2[t];
-    }
-    __threadfence();
-    __syncthreads();
-    __shared__ int s_last;
-    if (tid == 0) {
-        unsigned int prev = atomicAdd(&counters[a], 1u);
-        s_last = (prev == (unsigned int)(nseg - 1));
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        int64_t i = a * TT + t * BS + tid;
-        double s1 = 0.0, s2 = 0.0;
-        for (int o = 0; o < nseg; ++o) {
-            const double *pp = partials + ((a * plan.max_segments + o) * 2) * TT;
-            s1 += __ldcg(pp + t * BS + tid);
-            s2 += __ldcg(pp + TT + t * BS + tid);
-        }
-        if (i < N) {
-            y[i] = diag1 * u[i] - s1;
-            y[N + i] = diag2 * u[N + i] - s2;
-        }
-    }
-    if (tid == 0) counters[a] = 0u;   // ready for the next launch
-}
 
 // ---------------------------------------------------------------------------
 // FP32 pair arithmetic, FP32 partial sums per source tile, FP64 row sums.
@@ -962,7 +905,7 @@ matvec_sym64_kernel(const double *__restrict__ g64, const double *__restrict__ u
 
 pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision prec, const int *skip_flag) {
     const double diag1 = 0.5 * (1.0 + ctx->eps), diag2 = 0.5 * (1.0 + 1.0 / ctx->eps);
-    if (prec != PB_FP32PAIR && prec != PB_FP64)
+    if (prec != PB_FP32PAIR && prec != PB_FP64 && prec != PB_FLOAT2)
         return set_error(ctx, PB_ERR_ARG, "pb_matvec: unknown precision %d", (int)prec);
     {
         // the symmetric variants' scratch, allocated by the first product that needs it
@@ -1030,6 +973,9 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         }
 #undef PB_LAUNCH_F32X2
 #undef PB_LAUNCH_SYM
+    } else if (prec == PB_FLOAT2) {
+        pb_status fs = matvec_ff_enqueue(ctx, u, y, skip_flag);
+        if (fs != PB_OK) return fs;
     } else if (ctx->f64_variant == MV_F64_PLAIN) {
         F64Params prm{ctx->eps, 1.0 / ctx->eps, ctx->kappa, diag1, diag2};
         const StreamKPlan &pl = ctx->plan64;

@@ -196,7 +196,7 @@ pb_status load_charges(pb_ctx *ctx, const double *charges, int64_t nc) {
 }
 
 pb_status fill_opts(pb_ctx *ctx, const pb_solve_opts *in, pb_solve_opts *o) {
-    pb_solve_opts d{10, 1e-4, 1000, PB_FP32PAIR, 0};
+    pb_solve_opts d{10, 1e-4, 1000, PB_FP32PAIR, 0, PB_FP64};
     if (in) {
         d = *in;
         if (d.restart == 0) d.restart = 10;
@@ -207,7 +207,10 @@ pb_status fill_opts(pb_ctx *ctx, const pb_solve_opts *in, pb_solve_opts *o) {
         return set_error(ctx, PB_ERR_ARG, "restart must be in [1, %d], got %d", kMaxRestart, d.restart);
     if (!(d.tol > 0.0) || !isfinite(d.tol)) return set_error(ctx, PB_ERR_ARG, "tol must be > 0");
     if (d.maxit < 1) return set_error(ctx, PB_ERR_ARG, "maxit must be >= 1");
-    if (d.prec != PB_FP64 && d.prec != PB_FP32PAIR) return set_error(ctx, PB_ERR_ARG, "unknown precision");
+    if (d.prec != PB_FP64 && d.prec != PB_FP32PAIR && d.prec != PB_FLOAT2)
+        return set_error(ctx, PB_ERR_ARG, "unknown precision");
+    if (d.refine_prec != PB_FP64 && d.refine_prec != PB_FLOAT2)
+        return set_error(ctx, PB_ERR_ARG, "refine_prec must be PB_FP64 or PB_FLOAT2");
     if (d.refine < 0 || d.refine > 16) return set_error(ctx, PB_ERR_ARG, "refine must be in [0, 16]");
     *o = d;
     return PB_OK;
@@ -303,6 +306,10 @@ pb_status pb_create(const double *centroids, const double *normals, const double
         ctx->plan64 = make_plan(N, kF64TargetTile, kF64SourceTile, (int64_t)ctx->num_sms * matvec_occupancy(PB_FP64));
         ctx->partials_len = plan_partials(ctx->plan64, kF64TargetTile);
         ctx->counters_len = ctx->plan64.target_tiles;
+        ctx->planff = matvec_ff_plan(ctx);
+        if (plan_partials(ctx->planff, matvec_ff_target_tile()) > ctx->partials_len)
+            ctx->partials_len = plan_partials(ctx->planff, matvec_ff_target_tile());
+        if (ctx->planff.target_tiles > ctx->counters_len) ctx->counters_len = ctx->planff.target_tiles;
         for (int v = 1; v <= kNumF32Variants; ++v) {
             if (f32_variant_symmetric(v)) continue;   // own scratch, allocated when configured
             StreamKPlan pl = matvec_f32_plan(ctx, v, 0);
@@ -416,12 +423,12 @@ pb_status pb_solve(pb_ctx *ctx, const pb_solve_opts *opts, const double *x0, dou
     if (gs != PB_OK && gs != PB_ERR_NOCONV) return gs;
     int total_it = iters, total_cy = cycles, refined = 0;
     double rel64 = -1.0;
-    if (o.refine > 0 && o.prec != PB_FP64) {
+    if (o.refine > 0 && o.prec == PB_FP32PAIR) {
         if (!ctx->d && (s = ctx_alloc(ctx, (void **)&ctx->d, N2 * sizeof(double), "refinement d")) != PB_OK) return s;
         if (!ctx->rres && (s = ctx_alloc(ctx, (void **)&ctx->rres, N2 * sizeof(double), "refinement r")) != PB_OK) return s;
         for (int step = 0; step < o.refine; ++step) {
             // r = b - A_fp64 x ; A d = r ; x += d   (the FP64 product uses ctx->w)
-            if ((s = matvec_launch(ctx, ctx->x, ctx->rres, PB_FP64, nullptr)) != PB_OK) return s;
+            if ((s = matvec_launch(ctx, ctx->x, ctx->rres, o.refine_prec, nullptr)) != PB_OK) return s;
             if ((s = launch_sub(ctx, ctx->b, ctx->rres, ctx->rres)) != PB_OK) return s;
             pb_solve_opts oi = o;
             int it2 = 0, cy2 = 0;
@@ -436,7 +443,7 @@ pb_status pb_solve(pb_ctx *ctx, const pb_solve_opts *opts, const double *x0, dou
             total_cy += cy2;
             refined += 1;
         }
-        if ((s = matvec_launch(ctx, ctx->x, ctx->rres, PB_FP64, nullptr)) != PB_OK) return s;
+        if ((s = matvec_launch(ctx, ctx->x, ctx->rres, o.refine_prec, nullptr)) != PB_OK) return s;
         if ((s = launch_sub(ctx, ctx->b, ctx->rres, ctx->rres)) != PB_OK) return s;
         if ((s = norm2_launch(ctx, ctx->rres, N2, ctx->scalar + 1)) != PB_OK) return s;
         if ((s = norm2_launch(ctx, ctx->b, N2, ctx->scalar + 2)) != PB_OK) return s;

@@ -152,6 +152,8 @@ struct pb_ctx {
     pb::SymPlan plansym{};
     void *sym_scratch = nullptr;
     int64_t sym_scratch_len = 0;   // bytes
+    // float-float product plan (PB_FLOAT2; shares partials and tile counters)
+    pb::StreamKPlan planff{};
     // FP64 product variant (Matvec64Variant) and the symmetric one's plan and scratch
     int f64_variant = 1;
     pb::SymPlan plansym64{};
@@ -227,6 +229,10 @@ pb_status matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm);
 // allocates the scratch the configured FP32 variant needs (on ctx->stream), so
 // that later products allocate nothing (for example inside a stream capture)
 pb_status matvec_prepare(pb_ctx *ctx);
+// matvec_ff.cu: the float-float product (PB_FLOAT2)
+StreamKPlan matvec_ff_plan(pb_ctx *ctx);
+int matvec_ff_target_tile();
+pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *skip_flag);
 // FP64 product variant (Matvec64Variant); the symmetric ones allocate their
 // scratch with their first product
 pb_status matvec_configure_fp64(pb_ctx *ctx, int variant);

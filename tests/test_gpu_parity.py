@@ -82,6 +82,19 @@ def test_matvec_fp64_matches_oracle(name, surf, kappa, variant):
     assert np.max(np.abs(y - ref)) <= 1e-9 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("name,surf", SURFACES, ids=[s[0] for s in SURFACES])
+@pytest.mark.parametrize("kappa", [0.1257, 0.0])
+def test_matvec_float2_matches_oracle(name, surf, kappa):
+    """Float-float pair arithmetic on the FP32 pipe: the FP64 bound."""
+    u = _u(surf.n, 5)
+    with _ctx(surf, kappa=kappa) as ctx:
+        y = _gpu_matvec(ctx, u, "float2")
+    ref = oracle.matvec(surf, 80.0, kappa, u)
+    assert np.all(np.isfinite(y))
+    assert np.linalg.norm(y - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert np.max(np.abs(y - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
 F32_VARIANTS = [1, 2, 3, 4, 5, 6]   # scalar T4, packed f32x2 T2, T4, T3, symmetric T2, T4
 
 
@@ -181,13 +194,14 @@ def test_autotune_picks_a_valid_variant_with_the_same_result():
             pb.pb_matvec_configure(ctx, 7, 0)
 
 
-PREC_VARIANTS = [("fp64", v) for v in F64_VARIANTS] + [("fp32pair", v) for v in F32_VARIANTS]
+PREC_VARIANTS = ([("fp64", v) for v in F64_VARIANTS] + [("fp32pair", v) for v in F32_VARIANTS]
+                 + [("float2", 0)])
 
 
 def _configure(ctx, prec, variant):
     if prec == "fp64":
         _pb().pb_matvec_configure_fp64(ctx, variant)
-    else:
+    elif prec == "fp32pair":
         _pb().pb_matvec_configure(ctx, variant, 0)
 
 
@@ -221,7 +235,7 @@ def test_duplicate_centroids_are_dropped_like_the_self_term(prec, variant):
         _configure(ctx, prec, variant)
         y = _gpu_matvec(ctx, u, prec)
     ref = oracle.matvec(surf, 80.0, 0.1257, u)
-    tol = 1e-10 if prec == "fp64" else 2e-5
+    tol = 2e-5 if prec == "fp32pair" else 1e-10
     assert np.all(np.isfinite(y))
     assert np.linalg.norm(y - ref) <= tol * np.linalg.norm(ref)
 
@@ -303,6 +317,31 @@ def test_refinement_reaches_fp64_residual():
     assert refined.rel_resid_fp64 <= 1e-8
     assert abs(refined.energy_kcal - ref.energy_kcal) <= abs(plain.energy_kcal - ref.energy_kcal) + 1e-12 * abs(ref.energy_kcal)
     assert refined.energy_kcal == pytest.approx(ref.energy_kcal, rel=1e-8)
+
+
+def test_refinement_with_float2_residual_reaches_fp64_residual():
+    pb = _pb()
+    p = _problems()[0]
+    with _ctx(p.surface, p.charges, p.eps1, p.eps2, p.kappa) as ctx:
+        ref = pb.pb_solve(ctx, restart=10, tol=1e-12, maxit=2000, prec="fp64")
+        refined = pb.pb_solve(ctx, restart=10, tol=1e-9, maxit=2000, prec="fp32pair", refine=2,
+                              refine_prec="float2")
+        ff = pb.pb_solve(ctx, restart=10, tol=1e-11, maxit=2000, prec="float2")
+    assert refined.refine_steps == 2
+    assert refined.rel_resid_fp64 <= 1e-8
+    assert refined.energy_kcal == pytest.approx(ref.energy_kcal, rel=1e-8)
+    assert ff.energy_kcal == pytest.approx(ref.energy_kcal, rel=1e-9)
+
+
+def test_float2_is_rejected_where_it_has_no_meaning():
+    pb = _pb()
+    surf = pi.icosphere(2.0, 1)
+    with _ctx(surf, np.array([[0.0, 0.0, 0.0, 1.0]])) as ctx:
+        b = torch.empty(2 * surf.n, dtype=torch.float64, device="cuda")
+        with pytest.raises(pb.PBError):
+            pb.pb_source(ctx, b, "float2")
+        with pytest.raises(pb.PBError):
+            pb.pb_solve(ctx, prec="fp32pair", refine=1, refine_prec="fp32pair")
 
 
 def test_warm_start_takes_fewer_iterations():
