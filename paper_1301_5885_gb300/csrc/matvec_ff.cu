@@ -79,7 +79,7 @@ struct FFParams {
 __device__ __forceinline__ ff ff_exp2(ff t, const FFParams &p) {
     const float n = rintf(t.h);
     const ff f = fast_two_sum(t.h - n, t.l);
-    const float kf = rintf(f.h * 64.f);
+    const float kf = fminf(fmaxf(rintf(f.h * 64.f), -32.f), 32.f);   // |f| <= 1/2; the clamp bounds the index
     const ff g = fast_two_sum(f.h - kf * (1.f / 64.f), f.l);
     const ff u = ff_mul(g, p.ln2);
     const float r = fmaf(fmaf(u.h, 1.f / 720.f, 1.f / 120.f), u.h, 1.f / 24.f);
