@@ -4,7 +4,7 @@
 // two FP32 numbers (hi + lo, about 44 significant bits), with the error-free
 // transformations two-sum and two-product (the latter from one fused
 // multiply-add); the row sums go to FP64 once per staged source tile.  This
-// keeps the relative error of each pair term near 1e-12 while running on the
+// keeps the error of each pair term near 1e-12 of its size while running on the
 // FP32 pipe, which on GB300 retires many times the FP64 rate: it serves the
 // FP64 residual of iterative refinement and FP64-accuracy products.
 //
@@ -13,7 +13,10 @@
 // |g| <= 1/128: the table holds 2^(k/64) as float-float numbers, the last
 // factor is a degree-6 Taylor polynomial in u = g ln 2 (|u| < 0.0055, so the
 // truncation error is below 4e-17), with its low-order terms in float-float.
-// 1/rho comes from the MUFU rsqrt and one Newton step in float-float.
+// 1/rho comes from the MUFU rsqrt and one Newton step in float-float.  Sums
+// that can cancel (x_i - x_j, 1 - e, eps e' - 1, e'/eps - 1, e' - 1,
+// e p3 - 3 and the two parts of K4) are added accurately; the others with
+// the quicker sum.
 #include <math.h>
 
 #include <mutex>
@@ -51,6 +54,14 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
     s.l += t.l;
     return fast_two_sum(s.h, s.l);
 }
+// quick sum: error bounded relative to |a| + |b| (not to |a + b|); used where
+// no cancellation has to be resolved (sums of squares, dot products, row
+// accumulation, polynomial steps)
+__device__ __forceinline__ ff ff_add_q(ff a, ff b) {
+    ff s = two_sum(a.h, b.h);
+    s.l += a.l + b.l;
+    return fast_two_sum(s.h, s.l);
+}
 __device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.h, -a.l}; }
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {
@@ -84,9 +95,9 @@ __device__ __forceinline__ ff ff_exp2(ff t, const FFParams &p) {
     const ff u = ff_mul(g, p.ln2);
     const float r = fmaf(fmaf(u.h, 1.f / 720.f, 1.f / 120.f), u.h, 1.f / 24.f);
     const float t1 = fmaf(u.h, r, 1.f / 6.f);
-    const ff t2 = ff_add(ff{0.5f, 0.f}, ff_mulf(u, t1));
-    const ff t3 = ff_add(ff{1.f, 0.f}, ff_mul(u, t2));
-    const ff pe = ff_add(ff{1.f, 0.f}, ff_mul(u, t3));
+    const ff t2 = ff_add_q(ff{0.5f, 0.f}, ff_mulf(u, t1));
+    const ff t3 = ff_add_q(ff{1.f, 0.f}, ff_mul(u, t2));
+    const ff pe = ff_add_q(ff{1.f, 0.f}, ff_mul(u, t3));
     const float2 tk = c_exp2_table[(int)kf + 32];
     const ff e = ff_mul(pe, ff{tk.x, tk.y});
     const int ni = (int)n;
@@ -160,33 +171,34 @@ matvec_ff_kernel(const double *__restrict__ g64, const double *__restrict__ u, i
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
                     const ff dx = ff_sub(xi[t], sx), dy = ff_sub(yi[t], sy), dz = ff_sub(zi[t], sz);
-                    const ff r2 = ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
+                    const ff r2 = ff_add_q(ff_add_q(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
                     if (r2.h > 0.f) {      // the self pair and pairs at zero distance are dropped
                         // 1/rho: MUFU rsqrt, then one Newton step in float-float
                         const float y0 = rsqrt_approx(r2.h);
                         const float y0y0 = y0 * y0;
                         const ff yy{y0y0, fmaf(y0, y0, -y0y0)};
                         const ff h = ff_mul(r2, yy);
-                        const ff corr = ff_add(ff{1.5f, 0.f}, ff{-0.5f * h.h, -0.5f * h.l});
+                        const ff corr = ff_add_q(ff{1.5f, 0.f}, ff{-0.5f * h.h, -0.5f * h.l});
                         const ff inv = ff_mulf(corr, y0);
                         const ff rho = ff_mul(r2, inv);
                         const ff inv2 = ff_mul(inv, inv);
                         const ff inv3 = ff_mul(inv2, inv);
-                        const ff cx = ff_add(ff_add(ff_mul(dx, nxi[t]), ff_mul(dy, nyi[t])), ff_mul(dz, nzi[t]));
-                        const ff cy = ff_add(ff_add(ff_mul(dx, snx), ff_mul(dy, sny)), ff_mul(dz, snz));
-                        const ff nn = ff_add(ff_add(ff_mul(nxi[t], snx), ff_mul(nyi[t], sny)), ff_mul(nzi[t], snz));
+                        const ff cx = ff_add_q(ff_add_q(ff_mul(dx, nxi[t]), ff_mul(dy, nyi[t])), ff_mul(dz, nzi[t]));
+                        const ff cy = ff_add_q(ff_add_q(ff_mul(dx, snx), ff_mul(dy, sny)), ff_mul(dz, snz));
+                        const ff nn =
+                            ff_add_q(ff_add_q(ff_mul(nxi[t], snx), ff_mul(nyi[t], sny)), ff_mul(nzi[t], snz));
                         const ff kr = ff_mul(prm.kappa, rho);
                         const ff e = ff_exp2(ff_mul(prm.neg_kappa_log2e, rho), prm);
-                        const ff e1 = ff_add(e, ff_mul(e, kr));                          // e (1 + kappa rho)
+                        const ff e1 = ff_add_q(e, ff_mul(e, kr));                        // e (1 + kappa rho)
                         const ff k1 = ff_mul(ff_sub(one, e), inv);
                         const ff k2 = ff_mul(ff_mul(ff_sub(ff_mul(prm.eps, e1), one), cy), inv3);
                         const ff k3 = ff_mul(ff_mul(ff_sub(ff_mul(prm.inv_eps, e1), one), cx), inv3);
-                        const ff p3 = ff_add(ff_add(three, ff_mulf(kr, 3.f)), ff_mul(kr, kr));
+                        const ff p3 = ff_add_q(ff_add_q(three, ff_mulf(kr, 3.f)), ff_mul(kr, kr));
                         const ff e3 = ff_sub(ff_mul(e, p3), three);
                         const ff k4 = ff_mul(ff_sub(ff_mul(ff_sub(e1, one), nn), ff_mul(ff_mul(ff_mul(e3, cx), cy), inv2)),
                                              inv3);
-                        f1[t] = ff_add(f1[t], ff_add(ff_mul(k1, wpsi), ff_mul(k2, wphi)));
-                        f2[t] = ff_add(f2[t], ff_add(ff_mul(k3, wpsi), ff_mul(k4, wphi)));
+                        f1[t] = ff_add_q(f1[t], ff_add_q(ff_mul(k1, wpsi), ff_mul(k2, wphi)));
+                        f2[t] = ff_add_q(f2[t], ff_add_q(ff_mul(k3, wpsi), ff_mul(k4, wphi)));
                     }
                 }
             }
