@@ -61,9 +61,13 @@ typedef enum {
                              bits; about 1e-12 relative per pair term) on the
                              FP32 pipe, FP64 row sums: FP64-level products at
                              several times the FP64 kernel's speed where the
-                             FP64 rate is a small fraction of FP32.  Accepted
-                             by pb_matvec and pb_solve (prec, refine_prec);
-                             pb_source and pb_energy_of reject it. */
+                             FP64 rate is a small fraction of FP32.  From
+                             N = 2,048 each unordered pair is evaluated once
+                             for both rows, with device scratch of about
+                             8 N^2 / 256 bytes allocated by the first such
+                             product.  Accepted by pb_matvec and pb_solve
+                             (prec, refine_prec); pb_source and pb_energy_of
+                             reject it. */
 } pb_precision;
 
 typedef struct {

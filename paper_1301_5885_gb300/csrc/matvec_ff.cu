@@ -24,6 +24,7 @@
 #include "fastmath.cuh"
 #include "finish.cuh"
 #include "pb_internal.cuh"
+#include "sym.cuh"
 
 namespace pb {
 namespace {
@@ -104,6 +105,44 @@ __device__ __forceinline__ ff ff_exp2(ff t, const FFParams &p) {
     return ff{ldexpf(e.h, ni), ldexpf(e.l, ni)};
 }
 
+// K1..K4 ingredients of one pair in float-float: K1 = k1, K2 = a c_y,
+// K3 = b c_x, K4 = k4 (a, b and k4 already divided by rho^3).  Returns false
+// for a pair at zero distance (the self pair), which is dropped.
+struct FFPair {
+    ff k1, a, b, k4, cx, cy;
+};
+
+__device__ __forceinline__ bool ff_pair(ff xi, ff yi, ff zi, ff nxi, ff nyi, ff nzi, ff sx, ff sy, ff sz, ff snx,
+                                        ff sny, ff snz, const FFParams &prm, FFPair &o) {
+    const ff one{1.f, 0.f}, three{3.f, 0.f};
+    const ff dx = ff_sub(xi, sx), dy = ff_sub(yi, sy), dz = ff_sub(zi, sz);
+    const ff r2 = ff_add_q(ff_add_q(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
+    if (!(r2.h > 0.f)) return false;
+    // 1/rho: MUFU rsqrt, then one Newton step in float-float
+    const float y0 = rsqrt_approx(r2.h);
+    const float y0y0 = y0 * y0;
+    const ff yy{y0y0, fmaf(y0, y0, -y0y0)};
+    const ff h = ff_mul(r2, yy);
+    const ff corr = ff_add_q(ff{1.5f, 0.f}, ff{-0.5f * h.h, -0.5f * h.l});
+    const ff inv = ff_mulf(corr, y0);
+    const ff rho = ff_mul(r2, inv);
+    const ff inv2 = ff_mul(inv, inv);
+    const ff inv3 = ff_mul(inv2, inv);
+    o.cx = ff_add_q(ff_add_q(ff_mul(dx, nxi), ff_mul(dy, nyi)), ff_mul(dz, nzi));
+    o.cy = ff_add_q(ff_add_q(ff_mul(dx, snx), ff_mul(dy, sny)), ff_mul(dz, snz));
+    const ff nn = ff_add_q(ff_add_q(ff_mul(nxi, snx), ff_mul(nyi, sny)), ff_mul(nzi, snz));
+    const ff kr = ff_mul(prm.kappa, rho);
+    const ff e = ff_exp2(ff_mul(prm.neg_kappa_log2e, rho), prm);
+    const ff e1 = ff_add_q(e, ff_mul(e, kr));                        // e (1 + kappa rho)
+    o.k1 = ff_mul(ff_sub(one, e), inv);
+    o.a = ff_mul(ff_sub(ff_mul(prm.eps, e1), one), inv3);
+    o.b = ff_mul(ff_sub(ff_mul(prm.inv_eps, e1), one), inv3);
+    const ff p3 = ff_add_q(ff_add_q(three, ff_mulf(kr, 3.f)), ff_mul(kr, kr));
+    const ff e3 = ff_sub(ff_mul(e, p3), three);
+    o.k4 = ff_mul(ff_sub(ff_mul(ff_sub(e1, one), nn), ff_mul(ff_mul(ff_mul(e3, o.cx), o.cy), inv2)), inv3);
+    return true;
+}
+
 constexpr int kFFThreads = 128;
 constexpr int kFFTargets = 2;
 constexpr int kFFTargetTile = kFFThreads * kFFTargets;
@@ -125,8 +164,6 @@ matvec_ff_kernel(const double *__restrict__ g64, const double *__restrict__ u, i
     const int64_t S = plan.source_tiles;
     int64_t p = sk_begin(c, plan.work, plan.ctas);
     const int64_t pend = sk_begin(c + 1, plan.work, plan.ctas);
-    const ff one{1.f, 0.f}, three{3.f, 0.f};
-
     while (p < pend) {
         const int64_t a = p / S;
         const int64_t s_first = p % S;
@@ -170,35 +207,11 @@ matvec_ff_kernel(const double *__restrict__ g64, const double *__restrict__ u, i
                 const ff wpsi{q3.x, q3.y}, wphi{q3.z, q3.w};
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
-                    const ff dx = ff_sub(xi[t], sx), dy = ff_sub(yi[t], sy), dz = ff_sub(zi[t], sz);
-                    const ff r2 = ff_add_q(ff_add_q(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
-                    if (r2.h > 0.f) {      // the self pair and pairs at zero distance are dropped
-                        // 1/rho: MUFU rsqrt, then one Newton step in float-float
-                        const float y0 = rsqrt_approx(r2.h);
-                        const float y0y0 = y0 * y0;
-                        const ff yy{y0y0, fmaf(y0, y0, -y0y0)};
-                        const ff h = ff_mul(r2, yy);
-                        const ff corr = ff_add_q(ff{1.5f, 0.f}, ff{-0.5f * h.h, -0.5f * h.l});
-                        const ff inv = ff_mulf(corr, y0);
-                        const ff rho = ff_mul(r2, inv);
-                        const ff inv2 = ff_mul(inv, inv);
-                        const ff inv3 = ff_mul(inv2, inv);
-                        const ff cx = ff_add_q(ff_add_q(ff_mul(dx, nxi[t]), ff_mul(dy, nyi[t])), ff_mul(dz, nzi[t]));
-                        const ff cy = ff_add_q(ff_add_q(ff_mul(dx, snx), ff_mul(dy, sny)), ff_mul(dz, snz));
-                        const ff nn =
-                            ff_add_q(ff_add_q(ff_mul(nxi[t], snx), ff_mul(nyi[t], sny)), ff_mul(nzi[t], snz));
-                        const ff kr = ff_mul(prm.kappa, rho);
-                        const ff e = ff_exp2(ff_mul(prm.neg_kappa_log2e, rho), prm);
-                        const ff e1 = ff_add_q(e, ff_mul(e, kr));                        // e (1 + kappa rho)
-                        const ff k1 = ff_mul(ff_sub(one, e), inv);
-                        const ff k2 = ff_mul(ff_mul(ff_sub(ff_mul(prm.eps, e1), one), cy), inv3);
-                        const ff k3 = ff_mul(ff_mul(ff_sub(ff_mul(prm.inv_eps, e1), one), cx), inv3);
-                        const ff p3 = ff_add_q(ff_add_q(three, ff_mulf(kr, 3.f)), ff_mul(kr, kr));
-                        const ff e3 = ff_sub(ff_mul(e, p3), three);
-                        const ff k4 = ff_mul(ff_sub(ff_mul(ff_sub(e1, one), nn), ff_mul(ff_mul(ff_mul(e3, cx), cy), inv2)),
-                                             inv3);
-                        f1[t] = ff_add_q(f1[t], ff_add_q(ff_mul(k1, wpsi), ff_mul(k2, wphi)));
-                        f2[t] = ff_add_q(f2[t], ff_add_q(ff_mul(k3, wpsi), ff_mul(k4, wphi)));
+                    FFPair q;
+                    if (ff_pair(xi[t], yi[t], zi[t], nxi[t], nyi[t], nzi[t], sx, sy, sz, snx, sny, snz, prm, q)) {
+                        const ff k2 = ff_mul(q.a, q.cy), k3 = ff_mul(q.b, q.cx);
+                        f1[t] = ff_add_q(f1[t], ff_add_q(ff_mul(q.k1, wpsi), ff_mul(k2, wphi)));
+                        f2[t] = ff_add_q(f2[t], ff_add_q(ff_mul(k3, wpsi), ff_mul(q.k4, wphi)));
                     }
                 }
             }
@@ -213,15 +226,158 @@ matvec_ff_kernel(const double *__restrict__ g64, const double *__restrict__ u, i
     }
 }
 
+// The float-float product evaluated symmetrically: the tiling, plan and
+// finishing kernel of the symmetric FP32-pair and FP64 products, with each
+// unordered pair evaluated once in float-float for both rows (row j gets
+// K1 dphi_i - a c_x phi_i and -b c_y dphi_i + K4 phi_i).  Row sides are
+// summed in float-float per 128-source stage and then in FP64; a source's
+// column side is taken to FP64 and reduced over the warp with FP64 shuffles
+// and adds (the FP64 pipe is otherwise idle in this kernel).
+template <int T>
+__global__ void __launch_bounds__(kFFThreads)
+matvec_ffsym_kernel(const double *__restrict__ g64, const double *__restrict__ u, int64_t N, FFParams prm,
+                    SymPlan plan, double *__restrict__ islots, double *__restrict__ iside,
+                    double *__restrict__ jpart, const int *__restrict__ skip,
+                    unsigned long long *__restrict__ evaluated) {
+    constexpr int BS = kFFThreads, B = BS * T, TS = BS, NW = BS / 32, STAGES = B / TS;
+    if (skip != nullptr && *((volatile const int *)skip)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
+    __shared__ float4 s_p[TS][4];
+    __shared__ double s_col[NW][2][B];
+    const double *X = g64, *Y = g64 + N, *Z = g64 + 2 * N;
+    const double *NX = g64 + 3 * N, *NY = g64 + 4 * N, *NZ = g64 + 5 * N, *W = g64 + 6 * N;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool hi16 = (lane & 16) != 0;
+    const int64_t c = blockIdx.x;
+    const int64_t Tt = plan.tiles;
+    int64_t p = sk_begin(c, plan.work, plan.ctas);
+    const int64_t pend = sk_begin(c + 1, plan.work, plan.ctas);
+    const int64_t I_first = sym_row_of(p, Tt);
+
+    while (p < pend) {
+        const int64_t I = sym_row_of(p, Tt);
+        const int64_t row_end = sym_row_start(I + 1, Tt);
+        const int64_t p_stop = pend < row_end ? pend : row_end;
+        ff xi[T], yi[T], zi[T], nxi[T], nyi[T], nzi[T], wpi[T], wfi[T];
+        double acc1[T], acc2[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int64_t i0 = I * B + t * BS + tid;
+            const int64_t i = i0 < N ? i0 : N - 1;
+            xi[t] = ff_make(X[i]); yi[t] = ff_make(Y[i]); zi[t] = ff_make(Z[i]);
+            nxi[t] = ff_make(NX[i]); nyi[t] = ff_make(NY[i]); nzi[t] = ff_make(NZ[i]);
+            const double w = i0 < N ? W[i] * kInv4Pi : 0.0;
+            wpi[t] = ff_make(w * u[N + i]);
+            wfi[t] = ff_make(w * u[i]);
+            acc1[t] = 0.0;
+            acc2[t] = 0.0;
+        }
+        for (; p < p_stop; ++p) {
+            const int64_t J = I + (p - sym_row_start(I, Tt));
+            const bool diag = (J == I);
+            for (int stg = 0; stg < STAGES; ++stg) {
+                const int64_t s0 = J * B + stg * TS;
+                if (s0 >= N) break;
+                __syncthreads();
+                {
+                    const int64_t j = s0 + tid;
+                    if (j < N) {
+                        const ff x = ff_make(X[j]), yy = ff_make(Y[j]), z = ff_make(Z[j]);
+                        const ff nx = ff_make(NX[j]), ny = ff_make(NY[j]), nz = ff_make(NZ[j]);
+                        const double w = W[j] * kInv4Pi;
+                        const ff wpsi = ff_make(w * u[N + j]), wphi = ff_make(w * u[j]);
+                        s_p[tid][0] = make_float4(x.h, x.l, yy.h, yy.l);
+                        s_p[tid][1] = make_float4(z.h, z.l, nx.h, nx.l);
+                        s_p[tid][2] = make_float4(ny.h, ny.l, nz.h, nz.l);
+                        s_p[tid][3] = make_float4(wpsi.h, wpsi.l, wphi.h, wphi.l);
+                    }
+                }
+                __syncthreads();
+                const int cnt = (int)((N - s0) < TS ? (N - s0) : TS);
+                ff f1[T], f2[T];
+#pragma unroll
+                for (int t = 0; t < T; ++t) { f1[t] = ff{0.f, 0.f}; f2[t] = ff{0.f, 0.f}; }
+                for (int jj = 0; jj < cnt; ++jj) {
+                    const float4 q0 = s_p[jj][0], q1 = s_p[jj][1], q2 = s_p[jj][2], q3 = s_p[jj][3];
+                    const ff sx{q0.x, q0.y}, sy{q0.z, q0.w}, sz{q1.x, q1.y};
+                    const ff snx{q1.z, q1.w}, sny{q2.x, q2.y}, snz{q2.z, q2.w};
+                    const ff wpsi{q3.x, q3.y}, wphi{q3.z, q3.w};
+                    ff g1{0.f, 0.f}, g2{0.f, 0.f};     // column side of source jj
+#pragma unroll
+                    for (int t = 0; t < T; ++t) {
+                        FFPair q;
+                        if (ff_pair(xi[t], yi[t], zi[t], nxi[t], nyi[t], nzi[t], sx, sy, sz, snx, sny, snz, prm, q)) {
+                            f1[t] = ff_add_q(f1[t], ff_add_q(ff_mul(q.k1, wpsi), ff_mul(ff_mul(q.a, q.cy), wphi)));
+                            f2[t] = ff_add_q(f2[t], ff_add_q(ff_mul(ff_mul(q.b, q.cx), wpsi), ff_mul(q.k4, wphi)));
+                            if (!diag) {
+                                g1 = ff_add_q(g1, ff_sub(ff_mul(q.k1, wpi[t]), ff_mul(ff_mul(q.a, q.cx), wfi[t])));
+                                g2 = ff_add_q(g2, ff_sub(ff_mul(q.k4, wfi[t]), ff_mul(ff_mul(q.b, q.cy), wpi[t])));
+                            }
+                        }
+                    }
+                    if (!diag) {
+                        // lanes 0-15 end with the warp's sum of g1, 16-31 of g2 (FP64)
+                        const double d1 = (double)g1.h + (double)g1.l, d2 = (double)g2.h + (double)g2.l;
+                        double keep = hi16 ? d2 : d1;
+                        keep += __shfl_xor_sync(0xffffffffu, hi16 ? d1 : d2, 16);
+                        keep += __shfl_xor_sync(0xffffffffu, keep, 8);
+                        keep += __shfl_xor_sync(0xffffffffu, keep, 4);
+                        keep += __shfl_xor_sync(0xffffffffu, keep, 2);
+                        keep += __shfl_xor_sync(0xffffffffu, keep, 1);
+                        if ((lane & 15) == 0) s_col[warp][lane >> 4][stg * TS + jj] = keep;
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    acc1[t] += (double)f1[t].h + (double)f1[t].l;
+                    acc2[t] += (double)f2[t].h + (double)f2[t].l;
+                }
+            }
+            if (!diag) {
+                __syncthreads();
+                double *dst = jpart + sym_offdiag_index(I, J, Tt) * 2 * B;
+                for (int x = tid; x < 2 * B; x += BS) {
+                    const int r = x / B, k = x - r * B;
+                    double v = s_col[0][r][k];
+#pragma unroll
+                    for (int w2 = 1; w2 < NW; ++w2) v += s_col[w2][r][k];
+                    dst[x] = v;
+                }
+            }
+        }
+        const int64_t c0 = sk_cta_of(sym_row_start(I, Tt), plan.work, plan.ctas);
+        const int64_t c1 = sk_cta_of(row_end - 1, plan.work, plan.ctas);
+        double *dst = (c0 == c1) ? iside + I * 2 * B : islots + (2 * c + (I == I_first ? 0 : 1)) * 2 * B;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            dst[t * BS + tid] = acc1[t];
+            dst[B + t * BS + tid] = acc2[t];
+        }
+    }
+}
+
 std::mutex g_table_mu;
 bool g_table_ready[64] = {};
 
 }  // namespace
 
+// the symmetric kernel from this N (below it the plain one balances better),
+// with 2 targets per thread from kFFSymT2MinN
+constexpr int64_t kFFSymMinN = 2048;
+constexpr int64_t kFFSymT2MinN = 16384;
+
 StreamKPlan matvec_ff_plan(pb_ctx *ctx) {
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, matvec_ff_kernel, kFFThreads, 0);
     if (occ < 1) occ = 1;
+    if (ctx->N >= kFFSymMinN) {
+        const int T = ctx->N >= kFFSymT2MinN ? 2 : 1;
+        int occs = 0;
+        if (T == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs, matvec_ffsym_kernel<2>, kFFThreads, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs, matvec_ffsym_kernel<1>, kFFThreads, 0);
+        if (occs < 1) occs = 1;
+        ctx->planffsym = make_sym_plan(ctx->N, kFFThreads * T, (int64_t)ctx->num_sms * occs);
+    }
     return make_plan(ctx->N, kFFTargetTile, kFFSourceTile, (int64_t)ctx->num_sms * occ);
 }
 
@@ -258,9 +414,44 @@ pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *
     prm.ln2 = mk(0.69314718055994530942);
     prm.diag1 = 0.5 * (1.0 + ctx->eps);
     prm.diag2 = 0.5 * (1.0 + 1.0 / ctx->eps);
-    const StreamKPlan &pl = ctx->planff;
-    matvec_ff_kernel<<<(unsigned)pl.ctas, kFFThreads, 0, ctx->stream>>>(
-        ctx->g64, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag, ctx->mv_count);
+    if (ctx->N < kFFSymMinN) {
+        const StreamKPlan &pl = ctx->planff;
+        matvec_ff_kernel<<<(unsigned)pl.ctas, kFFThreads, 0, ctx->stream>>>(
+            ctx->g64, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag, ctx->mv_count);
+        return PB_OK;
+    }
+    const SymPlan &sp = ctx->planffsym;
+    const int T = ctx->N >= kFFSymT2MinN ? 2 : 1;
+    const int B = kFFThreads * T;
+    const int64_t need = sym64_scratch_bytes(sp, B);
+    if (need > ctx->symff_scratch_len) {
+        // the symmetric kernel's scratch, allocated by its first product
+        if (ctx->symff_scratch) ctx_free(ctx, ctx->symff_scratch);
+        ctx->device_bytes -= ctx->symff_scratch_len;
+        ctx->symff_scratch = nullptr;
+        ctx->symff_scratch_len = 0;
+        pb_status s = ctx_alloc(ctx, &ctx->symff_scratch, (size_t)need, "symmetric float-float matvec scratch");
+        if (s != PB_OK) return s;
+        ctx->symff_scratch_len = need;
+    }
+    auto r256 = [](int64_t b) { return (b + 255) / 256 * 256; };
+    double *iside = (double *)ctx->symff_scratch;
+    double *islots = iside + r256(sp.tiles * 2 * B * (int64_t)sizeof(double)) / (int64_t)sizeof(double);
+    double *jpart = islots + r256(sp.ctas * 4 * B * (int64_t)sizeof(double)) / (int64_t)sizeof(double);
+    if (T == 2) {
+        matvec_ffsym_kernel<2><<<(unsigned)sp.ctas, kFFThreads, 0, ctx->stream>>>(
+            ctx->g64, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);
+        matvec_sym_finalize<2 * kFFThreads, double>
+            <<<dim3((unsigned)sp.tiles, 2 * kFFThreads / kSymFinRows), kSymFinThreads, 0, ctx->stream>>>(
+                u, ctx->N, prm.diag1, prm.diag2, sp, islots, iside, jpart, y, skip_flag);
+    } else {
+        matvec_ffsym_kernel<1><<<(unsigned)sp.ctas, kFFThreads, 0, ctx->stream>>>(
+            ctx->g64, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);
+        matvec_sym_finalize<kFFThreads, double>
+            <<<dim3((unsigned)sp.tiles, kFFThreads / kSymFinRows), kSymFinThreads, 0, ctx->stream>>>(
+                u, ctx->N, prm.diag1, prm.diag2, sp, islots, iside, jpart, y, skip_flag);
+    }
+    PB_LAUNCHED();   // the finishing kernel (the caller counts the first)
     return PB_OK;
 }
 

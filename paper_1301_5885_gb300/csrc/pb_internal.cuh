@@ -152,8 +152,12 @@ struct pb_ctx {
     pb::SymPlan plansym{};
     void *sym_scratch = nullptr;
     int64_t sym_scratch_len = 0;   // bytes
-    // float-float product plan (PB_FLOAT2; shares partials and tile counters)
+    // float-float product (PB_FLOAT2): the plain plan (shares partials and
+    // tile counters) and the symmetric one's plan and scratch
     pb::StreamKPlan planff{};
+    pb::SymPlan planffsym{};
+    void *symff_scratch = nullptr;
+    int64_t symff_scratch_len = 0;
     // FP64 product variant (Matvec64Variant) and the symmetric one's plan and scratch
     int f64_variant = 1;
     pb::SymPlan plansym64{};

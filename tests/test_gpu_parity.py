@@ -95,6 +95,23 @@ def test_matvec_float2_matches_oracle(name, surf, kappa):
     assert np.max(np.abs(y - ref)) <= 1e-9 * np.max(np.abs(ref))
 
 
+def test_matvec_float2_symmetric_two_targets_matches_oracle():
+    """From N = 16,384 the float-float product is the symmetric kernel with
+    two targets per thread; ragged last tile, rows split over CTAs."""
+    surf = pi.icosphere(8.0, 5)
+    surf = surf.subset(np.arange(surf.n - 61))
+    u = _u(surf.n, 15)
+    with _ctx(surf) as ctx:
+        y1 = _gpu_matvec(ctx, u, "float2")
+        y2 = _gpu_matvec(ctx, u, "float2")
+        y64 = _gpu_matvec(ctx, u, "fp64")
+    ref = oracle.matvec(surf, 80.0, 0.1257, u)
+    assert np.array_equal(y1, y2)
+    assert np.linalg.norm(y1 - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert np.max(np.abs(y1 - ref)) <= 1e-9 * np.max(np.abs(ref))
+    assert np.linalg.norm(y1 - y64) <= 1e-10 * np.linalg.norm(ref)
+
+
 F32_VARIANTS = [1, 2, 3, 4, 5, 6]   # scalar T4, packed f32x2 T2, T4, T3, symmetric T2, T4
 
 
