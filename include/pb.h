@@ -128,7 +128,10 @@ pb_status pb_source(pb_ctx *ctx, double *b, pb_precision prec);
 
 /* y = A u, Eqs. (12)-(13).  u, y: device, 2N each, must not overlap.  Enqueued
  * on the context's stream.  Uses the context's scratch memory, so calls on one
- * context are serialised by its stream. */
+ * context are serialised by its stream.  prec: PB_FP32PAIR (the kernel chosen
+ * by pb_matvec_configure), PB_FP64 (the one chosen by
+ * pb_matvec_configure_fp64) or PB_FLOAT2; a symmetric kernel's scratch is
+ * allocated by its first product (PB_ERR_OOM if that fails). */
 pb_status pb_matvec(pb_ctx *ctx, const double *u, double *y, pb_precision prec);
 
 /* Solve A u = b with restarted GMRES on the device (Section 2.4; x0 = 0 unless
