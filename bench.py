@@ -75,6 +75,7 @@ MATVEC_TRAFFIC_BYTES = {
 WORKLOADS = {
     "sphere2": "Kirkwood sphere R=20 A, icosphere level 6 (81,920 triangles), 20 charges in 0.8R, "
                "eps 1/80, kappa 0.1257",
+    "sphere2_salt_free": "the sphere2 surface and charges with kappa = 0 (salt-free; the kappa = 0 kernels)",
     "sphere1": "Born sphere R=2 A, icosphere level 4 (5,120 triangles), one central charge, eps 1/80, kappa 0.1257",
     "protein300k": "protein-like 2,000-atom chain, probe-inflated Gaussian isosurface (~300k triangles)",
 }

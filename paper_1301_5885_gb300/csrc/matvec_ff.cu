@@ -231,8 +231,8 @@ matvec_ff_kernel(const double *__restrict__ g64, const double *__restrict__ u, i
 // unordered pair evaluated once in float-float for both rows (row j gets
 // K1 dphi_i - a c_x phi_i and -b c_y dphi_i + K4 phi_i).  Row sides are
 // summed in float-float per 128-source stage and then in FP64; a source's
-// column side is taken to FP64 and reduced over the warp with FP64 shuffles
-// and adds (the FP64 pipe is otherwise idle in this kernel).
+// column side is reduced over the warp in float-float (shuffling both parts)
+// and stored in FP64.
 template <int T>
 __global__ void __launch_bounds__(kFFThreads)
 matvec_ffsym_kernel(const double *__restrict__ g64, const double *__restrict__ u, int64_t N, FFParams prm,
@@ -316,15 +316,17 @@ matvec_ffsym_kernel(const double *__restrict__ g64, const double *__restrict__ u
                         }
                     }
                     if (!diag) {
-                        // lanes 0-15 end with the warp's sum of g1, 16-31 of g2 (FP64)
-                        const double d1 = (double)g1.h + (double)g1.l, d2 = (double)g2.h + (double)g2.l;
-                        double keep = hi16 ? d2 : d1;
-                        keep += __shfl_xor_sync(0xffffffffu, hi16 ? d1 : d2, 16);
-                        keep += __shfl_xor_sync(0xffffffffu, keep, 8);
-                        keep += __shfl_xor_sync(0xffffffffu, keep, 4);
-                        keep += __shfl_xor_sync(0xffffffffu, keep, 2);
-                        keep += __shfl_xor_sync(0xffffffffu, keep, 1);
-                        if ((lane & 15) == 0) s_col[warp][lane >> 4][stg * TS + jj] = keep;
+                        // lanes 0-15 end with the warp's sum of g1, 16-31 of g2,
+                        // summed in float-float (the FP64 pipe is far slower)
+                        ff keep = hi16 ? g2 : g1;
+                        const ff send = hi16 ? g1 : g2;
+                        keep = ff_add_q(keep, ff{__shfl_xor_sync(0xffffffffu, send.h, 16),
+                                                 __shfl_xor_sync(0xffffffffu, send.l, 16)});
+#pragma unroll
+                        for (int off = 8; off >= 1; off >>= 1)
+                            keep = ff_add_q(keep, ff{__shfl_xor_sync(0xffffffffu, keep.h, off),
+                                                     __shfl_xor_sync(0xffffffffu, keep.l, off)});
+                        if ((lane & 15) == 0) s_col[warp][lane >> 4][stg * TS + jj] = (double)keep.h + (double)keep.l;
                     }
                 }
 #pragma unroll

@@ -193,6 +193,8 @@ def by_name(name: str) -> Problem:
         return kirkwood_sphere_single()
     if name == "sphere2":
         return kirkwood_sphere_multi()
+    if name == "sphere2_salt_free":
+        return kirkwood_sphere_multi(kappa=0.0)
     if name == "protein300k":
         return protein_like()
     raise KeyError(name)
