@@ -416,9 +416,7 @@ __device__ __forceinline__ void sym_stage(const float4 *s_a, const float4 *s_b, 
     const int cbase = (lane >> 4) * B + ((lane >> 3) & 1);
     const bool writer = (lane & 7) == 0;
     WarpReduce4 red;
-    // the kappa = 0 body is less than half as long: unrolled further
-    constexpr int kUnroll = K0 ? 16 : 8;
-#pragma unroll kUnroll
+#pragma unroll 8
     for (int q = 0; q < npairs; ++q) {
         const float4 A = s_a[q], Bq = s_b[q], C = s_c[q], D = s_d[q];
         const float2 mx = make_float2(A.x, A.y), my = make_float2(A.z, A.w), mz = make_float2(Bq.x, Bq.y);
