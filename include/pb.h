@@ -163,6 +163,14 @@ const char *pb_last_error(const pb_ctx *ctx);
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t pb_kernel_launches(void);
 
+/* Device memory of contexts, batches and servers comes from a library-owned
+ * stream-ordered pool per device that keeps freed memory for reuse.  This
+ * returns the pool's unused memory of the current device to the driver
+ * (after synchronising the device) and frees the cached pinned host blocks
+ * that no context holds.  Memory in use is not affected.  A library
+ * convenience; the paper has no counterpart. */
+pb_status pb_release_cached_memory(void);
+
 /* Kernel timing for measurement (not part of the method).  While enabled,
  * every matrix-vector product launched by this context is bracketed by CUDA
  * events recorded on the context's stream.  pb_profile_read waits for the

@@ -85,6 +85,7 @@ SIGNATURES = {
     "pb_status_string": (ctypes.c_char_p, [_I]),
     "pb_last_error": (ctypes.c_char_p, [_VP]),
     "pb_kernel_launches": (ctypes.c_uint64, []),
+    "pb_release_cached_memory": (_I, []),
     "pb_profile_enable": (_I, [_VP, _I]),
     "pb_profile_read": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), ctypes.POINTER(_I64), _I]),
     "pb_matvec_f32_static": (_I, [_VP, _VP, _VP, _I64, ctypes.POINTER(_D), _D, _D, _D, _VP, _VP, _VP]),
@@ -145,6 +146,11 @@ def pb_last_error(ctx=None) -> str:
 
 def pb_kernel_launches() -> int:
     return int(lib().pb_kernel_launches())
+
+
+def pb_release_cached_memory() -> None:
+    """Return the library pool's unused device memory and cached pinned blocks."""
+    _check(lib().pb_release_cached_memory())
 
 
 def _check(status: int, ctx=None):

@@ -272,6 +272,24 @@ const char *pb_last_error(const pb_ctx *ctx) { return ctx ? ctx->last_error : g_
 
 uint64_t pb_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+pb_status pb_release_cached_memory(void) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_error(nullptr, e, "pb_release_cached_memory");
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (dev >= 0 && dev < 64) pool = g_pool[dev];
+    }
+    if (pool && (e = cudaMemPoolTrimTo(pool, 0)) != cudaSuccess)
+        return cuda_error(nullptr, e, "pb_release_cached_memory: trim");
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    for (auto &kv : g_pinned) cudaFreeHost(kv.second);
+    g_pinned.clear();
+    return PB_OK;
+}
+
 pb_status pb_create(const double *centroids, const double *normals, const double *areas, int64_t N,
                     const double *charges, int64_t Nc, double eps1, double eps2, double kappa, void *cuda_stream,
                     pb_ctx **out) {

@@ -361,6 +361,18 @@ def test_float2_is_rejected_where_it_has_no_meaning():
             pb.pb_solve(ctx, prec="fp32pair", refine=1, refine_prec="fp32pair")
 
 
+def test_cached_memory_release_keeps_live_contexts_working():
+    pb = _pb()
+    p = _problems()[0]
+    with _ctx(p.surface, p.charges, p.eps1, p.eps2, p.kappa) as ctx:
+        e1 = pb.pb_solve(ctx, tol=1e-8, prec="fp64").energy_kcal
+        with _ctx(p.surface, p.charges, p.eps1, p.eps2, p.kappa) as other:
+            pb.pb_solve(other, tol=1e-6)
+        pb.pb_release_cached_memory()
+        e2 = pb.pb_solve(ctx, tol=1e-8, prec="fp64").energy_kcal
+    assert e2 == pytest.approx(e1, rel=1e-12)
+
+
 def test_warm_start_takes_fewer_iterations():
     pb = _pb()
     p = _problems()[0]
