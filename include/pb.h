@@ -314,16 +314,20 @@ pb_status pb_matvec_configure_fp64(pb_ctx *ctx, int variant, int *variant_out);
  *    normals must already be unit length and areas > 0 (no validation pass);
  *  - center: host, 3 doubles subtracted from every centroid before the FP32
  *    cast (pass the bounding-box centre, as pb_create does; NULL = origin);
- *  - u, y: device, 2N FP64 each, must not overlap; the caller owns them;
+ *  - u, y: device, 2N FP64 each; the caller owns them.  y must not overlap
+ *    u or any geometry array (other CTAs still read them while y is written):
+ *    such calls are rejected with PB_ERR_ARG;
  *  - the work is enqueued on cuda_stream (NULL = legacy default stream).
  * Scratch lives in one 16 MiB file-scope static device array that every GPU
  * loading the library keeps until the process exits.  Its arrival counters are
  * cleared by every call; every call shares the array, so calls that overlap
- * on the GPU race and must not be issued.  The first call on a device resolves
- * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  N above 2^24 = 16,777,216
- * is rejected with PB_ERR_ARG (a fixed limit of the static scratch).  Errors:
- * PB_ERR_ARG, PB_ERR_CUDA; messages via pb_last_error(NULL). */
+ * on the GPU race and must not be issued.  Every call resolves the array's
+ * device address (cudaGetSymbolAddress, no allocation) with the caller's
+ * device current, and the first call on a device also queries its SM count
+ * and the kernel's occupancy; make that first call before any stream capture.
+ * N above 2^24 = 16,777,216 is rejected with PB_ERR_ARG (a fixed limit of the
+ * static scratch).  Errors: PB_ERR_ARG, PB_ERR_CUDA; messages via
+ * pb_last_error(NULL). */
 pb_status pb_matvec_f32_static(const double *centroids, const double *normals, const double *areas, int64_t N,
                                const double *center, double eps1, double eps2, double kappa, const double *u,
                                double *y, void *cuda_stream);

@@ -174,13 +174,18 @@ def gauss_sums(surface, points) -> np.ndarray:
 
 
 # --- GMRES ---------------------------------------------------------------------
-def gmres(apply_A, b, restart: int = 10, tol: float = 1e-10, maxit: int = 1000, x0=None):
+def gmres(apply_A, b, restart: int = 10, tol: float = 1e-10, maxit: int = 1000, x0=None,
+          callback=None):
     """Restarted GMRES(m) of Saad & Schultz: modified Gram-Schmidt Arnoldi, Givens
     rotations, back substitution, x += V y.  Unpreconditioned; starts from x0
     (zero by default) and restarts from the current approximation.  Stops when
     the true relative residual ||b - Ax|| / ||b|| <= tol, checked at every restart;
     inside a cycle the Givens estimate ends the cycle early.  One iteration is one
     Arnoldi step (one product with A).
+
+    ``callback(x, iterations, rel_resid)``, if given, is called after each true
+    residual (at every restart) and does not change the iteration: a run
+    restarted from that x continues exactly as the uninterrupted one would.
 
     Returns (x, iterations, history of true relative residuals, converged)."""
     b = _f64(b)
@@ -199,6 +204,8 @@ def gmres(apply_A, b, restart: int = 10, tol: float = 1e-10, maxit: int = 1000, 
         first = False
         beta = float(np.linalg.norm(r))
         history.append(beta / bnorm)
+        if callback is not None:
+            callback(x, iters, beta / bnorm)
         if not np.isfinite(beta):
             break
         if beta / bnorm <= tol:
@@ -246,11 +253,12 @@ def gmres(apply_A, b, restart: int = 10, tol: float = 1e-10, maxit: int = 1000, 
 
 
 def solve(surface, charges, eps1: float, eps2: float, kappa: float, restart: int = 10,
-          tol: float = 1e-10, maxit: int = 1000, x0=None) -> dict:
+          tol: float = 1e-10, maxit: int = 1000, x0=None, callback=None) -> dict:
     """b from Eq. (11), GMRES on Eqs. (12)-(13), E_sol from Eq. (14)."""
     eps = eps2 / eps1
     b = source(surface, charges, eps1)
-    u, iters, hist, conv = gmres(lambda v: matvec(surface, eps, kappa, v), b, restart, tol, maxit, x0)
+    u, iters, hist, conv = gmres(lambda v: matvec(surface, eps, kappa, v), b, restart, tol, maxit, x0,
+                                 callback)
     E = reaction_energy(surface, charges, eps, kappa, u)
     return {"u": u, "b": b, "energy": E, "iters": iters, "history": hist, "converged": conv}
 

@@ -18,8 +18,10 @@
 // row sums, deterministic last-arriver reduction); only the input layout
 // (FP64 arrays, converted while staging) and the home of the scratch differ.
 #include <math.h>
+#include <stdint.h>
 #include <mutex>
 
+#include "fastmath.cuh"
 #include "pb_internal.cuh"
 
 namespace pb {
@@ -35,9 +37,12 @@ constexpr int64_t kStaticMaxN = int64_t(1) << 24;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
+// Per-device launch shape, filled by the first call on a device.  The scratch
+// address is not cached: it is resolved on every call, so that a module
+// reloaded after cudaDeviceReset (which may place the array elsewhere) is
+// still addressed correctly.
 struct DeviceSetup {
     bool ready = false;
-    unsigned char *scratch = nullptr;   // device address of g_static_scratch on this device
     int num_sms = 0;
     int occupancy = 0;
 };
@@ -45,18 +50,6 @@ std::mutex g_setup_mu;
 DeviceSetup g_setup[kMaxDevices];
 
 constexpr int BS = kF32Threads, T = kF32TargetsPerThread, TT = kF32TargetTile, TS = kF32SourceTile;
-
-__device__ __forceinline__ float rsqrt_approx_s(float x) {
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ float exp2_approx_s(float x) {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 struct StaticParams {
     float eps, inv_eps, kappa, neg_kappa_log2e;
@@ -124,10 +117,10 @@ matvec_f32_static_kernel(const double *__restrict__ c, const double *__restrict_
                 for (int t = 0; t < T; ++t) {
                     const float dx = xi[t] - sp.x, dy = yi[t] - sp.y, dz = zi[t] - sp.z;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    float inv = rsqrt_approx_s(r2);
+                    float inv = rsqrt_approx(r2);
                     inv = (r2 > 0.f) ? inv : 0.f;
                     const float rho = r2 * inv;
-                    const float e = exp2_approx_s(prm.neg_kappa_log2e * rho);
+                    const float e = exp2_approx(prm.neg_kappa_log2e * rho);
                     const float kr = prm.kappa * rho;
                     const float e1 = fmaf(e, kr, e);
                     const float inv2 = inv * inv;
@@ -202,6 +195,12 @@ matvec_f32_static_kernel(const double *__restrict__ c, const double *__restrict_
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// true when the byte ranges [a, a + na) and [b, b + nb) intersect
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb) {
+    const uintptr_t pa = (uintptr_t)a, pb_ = (uintptr_t)b;
+    return pa < pb_ + nb && pb_ < pa + na;
+}
+
 }  // namespace
 }  // namespace pb
 
@@ -215,11 +214,18 @@ extern "C" pb_status pb_matvec_f32_static(const double *centroids, const double 
     if (N < 1) return set_error(nullptr, PB_ERR_ARG, "pb_matvec_f32_static: N must be >= 1");
     if (!(eps1 > 0.0) || !(eps2 > 0.0) || !isfinite(eps1) || !isfinite(eps2) || !(kappa >= 0.0) || !isfinite(kappa))
         return set_error(nullptr, PB_ERR_ARG, "pb_matvec_f32_static: need eps1 > 0, eps2 > 0, kappa >= 0 (finite)");
-    if (u == y) return set_error(nullptr, PB_ERR_ARG, "pb_matvec_f32_static: u and y must not overlap");
     if (N > kStaticMaxN)
         return set_error(nullptr, PB_ERR_ARG,
                          "pb_matvec_f32_static: N = %lld exceeds the maximum %lld of the fixed static scratch",
                          (long long)N, (long long)kStaticMaxN);
+    {
+        // y is written while other CTAs still read u and the geometry
+        const size_t n = (size_t)N * sizeof(double);
+        if (ranges_overlap(y, 2 * n, u, 2 * n) || ranges_overlap(y, 2 * n, centroids, 3 * n) ||
+            ranges_overlap(y, 2 * n, normals, 3 * n) || ranges_overlap(y, 2 * n, areas, n))
+            return set_error(nullptr, PB_ERR_ARG,
+                             "pb_matvec_f32_static: y must not overlap u, centroids, normals or areas");
+    }
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -228,25 +234,25 @@ extern "C" pb_status pb_matvec_f32_static(const double *centroids, const double 
         return set_error(nullptr, PB_ERR_ARG, "pb_matvec_f32_static: device ordinal %d out of range", dev);
     DeviceSetup su;
     {
-        // once per device, with that device current: resolve the device
-        // address of the static scratch array (host code must not use the
-        // symbol itself as a pointer) and size the persistent grid
+        // once per device, with that device current: size the persistent grid
         std::lock_guard<std::mutex> lock(g_setup_mu);
         DeviceSetup &g = g_setup[dev];
         if (!g.ready) {
-            void *addr = nullptr;
-            e = cudaGetSymbolAddress(&addr, g_static_scratch);
-            if (e != cudaSuccess) return cuda_error(nullptr, e, "pb_matvec_f32_static: cudaGetSymbolAddress");
             e = cudaDeviceGetAttribute(&g.num_sms, cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess) return cuda_error(nullptr, e, "pb_matvec_f32_static: device query");
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.occupancy, matvec_f32_static_kernel, BS, 0);
             if (e != cudaSuccess) return cuda_error(nullptr, e, "pb_matvec_f32_static: occupancy query");
             if (g.occupancy < 1) g.occupancy = 1;
-            g.scratch = (unsigned char *)addr;
             g.ready = true;
         }
         su = g;
     }
+    // the device address of the static scratch array on the current device
+    // (host code must not use the symbol itself as a pointer); resolved on
+    // every call, which allocates nothing
+    unsigned char *scratch = nullptr;
+    e = cudaGetSymbolAddress((void **)&scratch, g_static_scratch);
+    if (e != cudaSuccess) return cuda_error(nullptr, e, "pb_matvec_f32_static: cudaGetSymbolAddress");
 
     // Persistent grid as for pb_matvec, capped so that two partial slots per
     // CTA fit in the static array after the counters.
@@ -259,8 +265,8 @@ extern "C" pb_status pb_matvec_f32_static(const double *centroids, const double 
     const StreamKPlan plan = make_plan(N, TT, TS, ctas);
 
     cudaStream_t stream = (cudaStream_t)cuda_stream;
-    unsigned int *counters = (unsigned int *)su.scratch;
-    double *partials = (double *)(su.scratch + counter_bytes);
+    unsigned int *counters = (unsigned int *)scratch;
+    double *partials = (double *)(scratch + counter_bytes);
     // the counters must start at zero; the array keeps the last call's contents
     e = cudaMemsetAsync(counters, 0, (size_t)target_tiles * sizeof(unsigned int), stream);
     if (e != cudaSuccess) return cuda_error(nullptr, e, "pb_matvec_f32_static: clearing counters");

@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 import pb_inputs as pi
+from blockcheck import TOL_FP32PAIR, TOL_FP64, assert_rows_close
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -94,12 +95,8 @@ def test_sampled_rows_at_full_size(which, sphere2):
     with _ctx(p) as ctx:
         ud = torch.tensor(u, device="cuda")
         y = torch.empty_like(ud)
-        for prec, tol in (("fp64", 1e-10), ("fp32pair", 2e-5)):
+        for prec, tol in (("fp64", TOL_FP64), ("float2", TOL_FP64), ("fp32pair", TOL_FP32PAIR)):
             pb.pb_matvec(ctx, ud, y, prec)
             torch.cuda.synchronize()
             yh = y.cpu().numpy()
-            g1, g2 = yh[rows], yh[p.n + rows]
-            ref = np.concatenate([r1, r2])
-            got = np.concatenate([g1, g2])
-            assert np.all(np.isfinite(got))
-            assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), prec
+            assert_rows_close(yh[rows], yh[p.n + rows], r1, r2, tol, prec)

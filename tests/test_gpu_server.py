@@ -8,6 +8,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 import pb_inputs as pi
 
 pytestmark = pytest.mark.gpu
@@ -75,6 +76,16 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         assert r["status"] == pb.PB_OK
         assert r["energy_kcal"] == pytest.approx(e_alone, rel=1e-6)
         assert 0.0 <= r["queue_ms"] <= r["latency_ms"]
+    # the mixed results meet the 1e-5 bound against the FP64 oracle (the
+    # requests small enough for a quick oracle solve: 320 to ~2,000 triangles)
+    checked = 0
+    for rid, p in zip(ids, reqs):
+        if p.n > 2500:
+            continue
+        ref = oracle.solve(p.surface, p.charges, p.eps1, p.eps2, p.kappa, tol=1e-11, maxit=2000)["energy"]
+        assert got[rid]["energy_kcal"] == pytest.approx(ref, rel=1e-5), p.name
+        checked += 1
+    assert checked >= 3
     # and the same as the one-at-a-time library solve
     for e_alone, p in zip(alone[:3], reqs[:3]):
         s = p.surface

@@ -133,6 +133,38 @@ def test_dense_assembly_and_lu_match_matrix_free_gmres(which):
     assert it["energy"] == pytest.approx(dense["energy"], rel=1e-10)
 
 
+@pytest.mark.parametrize("which", ["sphere", "solute"])
+def test_sampled_rows_equal_the_full_product_rows(which):
+    """oracle.matvec_rows (the reference of the full-size sampled-row parity
+    tests and of the CPU baseline) returns exactly rows i and N+i of the full
+    product, bit for bit (same summation order), in the right output slots:
+    the phi and psi halves of u are given scales 1 and 1000, so a swapped
+    slot or a swapped u[j] / u[N+j] cannot pass.  Rows 0 and N-1 included,
+    and a repeated row.  On the small case both also equal the dense A's
+    rows (brute force)."""
+    if which == "sphere":
+        p = pi.kirkwood_sphere_multi(level=4, radius=7.0, n_charges=3, seed=5)
+    else:
+        p = pi.protein_like(n_atoms=10, seed=3, target_triangles=None, spacing=1.9)
+    eps = p.eps2 / p.eps1
+    rng = np.random.Generator(np.random.PCG64(17))
+    u = np.concatenate([rng.normal(size=p.n), 1000.0 * rng.normal(size=p.n)])
+    rows = np.concatenate([[0, p.n - 1], rng.choice(p.n, 40, replace=False), [7, 7]])
+    full = oracle.matvec(p.surface, eps, p.kappa, u)
+    y1, y2 = oracle.matvec_rows(p.surface, eps, p.kappa, u, rows)
+    assert np.array_equal(y1, full[rows])
+    assert np.array_equal(y2, full[p.n + rows])
+    assert not np.allclose(y1, y2)
+    small = p.surface.subset(np.arange(0, p.n, max(1, p.n // 400)))
+    us = np.concatenate([rng.normal(size=small.n), 1000.0 * rng.normal(size=small.n)])
+    A = oracle.assemble(small, eps, p.kappa)
+    rs = np.array([0, small.n - 1, small.n // 2])
+    z1, z2 = oracle.matvec_rows(small, eps, p.kappa, us, rs)
+    dense = A @ us
+    assert np.allclose(z1, dense[rs], rtol=1e-12, atol=1e-12 * np.abs(dense).max())
+    assert np.allclose(z2, dense[small.n + rs], rtol=1e-12, atol=1e-12 * np.abs(dense).max())
+
+
 def test_gmres_matches_lu_on_a_random_nonsymmetric_system():
     rng = np.random.Generator(np.random.PCG64(8))
     n = 60
