@@ -553,6 +553,8 @@ def _clock_and_uuid(torch, dev):
     return ClockSampler(uuid)
 
 
+ROW_SUMS = {0: "fp64 registers", 1: "fp64 shared memory", 2: "float-float registers",
+            3: "float-float shared memory"}
 BATCH_FP32_OPS_PER_EVAL = 36     # K1..K4 of one pair, packed FP32 (kappa > 0; 2 MUFU besides)
 BATCH_FP32_OPS_PER_RHS = 4       # the two rows' accumulations per charge set
 
@@ -647,9 +649,11 @@ def run_batch(args):
         dev_in = [tuple(torch.tensor(a, device=dev) for a in (c, n, w, q)) for c, n, w, q in sols]
         ctxs = [pb.pb_create(c, n, w, q, 1.0, 80.0, 0.1257, stream=stream) for c, n, w, q in dev_in]
         ns = [c.n for c in ctxs]
+        warm_info = None
         for _ in range(args.warmup):
-            pb.pb_batch_solve(ctxs, variants, restart=args.restart, tol=args.tol, use_graph=True,
-                              raise_on_noconv=False)
+            _, wi = pb.pb_batch_solve(ctxs, variants, restart=args.restart, tol=args.tol, use_graph=True,
+                                      raise_on_noconv=False)
+            warm_info = warm_info or wi       # the first call tunes the product (untimed)
         stream.synchronize()
         sampler = _clock_and_uuid(torch, dev)
         sampler.start()
@@ -695,6 +699,12 @@ def run_batch(args):
                                    f"N {min(ns)}-{max(ns)}) x 8 charge variants, one lockstep batch per step",
                        "n_triangles_total": int(sum(ns)), "instances": int(infos[-1]["instances"]),
                        "gmres_restart": args.restart, "gmres_tol": args.tol, "cuda_graph": True,
+                       "product_shape": {"targets_per_thread": infos[-1]["targets_per_thread"],
+                                         "row_sums": ROW_SUMS.get(infos[-1]["row_sums"]),
+                                         "ctas_per_sm": infos[-1]["ctas_per_sm"] or "occupancy",
+                                         "autotuned": bool(warm_info and warm_info["tuned"]),
+                                         "tune_candidates": warm_info["tune_candidates"] if warm_info else 0,
+                                         "tune_ms": warm_info["tune_ms"] if warm_info else 0.0},
                        "l2": "flushed between steps (256 MiB write)"},
             "solves_per_s": nsolve / (total_ms * 1e-3),
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},

@@ -215,11 +215,49 @@ typedef struct {
     int64_t matvec_launches;
     double matvec_ms;     /* summed CUDA-event time of the product launches
                              (only measured when use_graph == 2) */
+    int targets_per_thread; /* shape of the batched product in the last cycle */
+    int row_sums;           /* PB_ROWSUM_* of that shape */
+    int ctas_per_sm;        /* 0: the kernel's occupancy */
+    int tuned;              /* 1 if the autotuner ran during this call */
+    int tune_candidates;    /* (shape, CTA count) pairs it timed */
+    double tune_ms;         /* host time it took */
 } pb_batch_info;
 
 pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double *const *charges, const int64_t *nc,
                          const int *nrhs, const pb_solve_opts *opts, int use_graph, double *energies,
                          pb_batch_info *info);
+
+/* Shapes of the batched product (a library extension; the paper has a single
+ * one-target-per-thread kernel).  A shape is (targets per thread, row sums):
+ * more targets per thread share each staged source among more targets; the
+ * row sums of every target row are kept in FP64 or in float-float (an
+ * unevaluated sum of two FP32 numbers, about 48 significant bits), in
+ * registers or in the thread's shared-memory slots.  Every shape computes the
+ * same Eqs. (12)-(13) with FP32 pair terms summed per 256-source stage; they
+ * differ only in summation arithmetic (results agree to the FP32-pair
+ * tolerance).  The third knob is the number of CTAs per SM.
+ *
+ * pb_batch_solve tunes by default: the first batch of a (width, size class)
+ * (size class: a quarter octave of the summed N^2 of its batched surfaces)
+ * times every instantiated shape at every CTA count on its own work list
+ * (two launches each after a warm-up) when its tables are built, and caches
+ * the fastest per device; later batches, and the solve server, use the cached
+ * choice of the nearest size class within an octave (the server never tunes
+ * inline), else the built-in default.  pb_batch_info reports the shape used.
+ *
+ * pb_batch_set_tuning: mode 1 = as above (default); 0 = built-in defaults only.
+ * pb_batch_force_shape: use (targets_per_thread, row_sums, ctas_per_sm) for
+ *   every batch of this width; targets_per_thread = 0 removes the override.
+ *   PB_ERR_ARG for a shape that is not instantiated.
+ * pb_batch_clear_tuning: forget the cached choices.
+ * pb_batch_shapes: the instantiated shapes of a width (the default first);
+ *   returns their number, writes at most max_out. */
+enum { PB_ROWSUM_FP64_REGISTERS = 0, PB_ROWSUM_FP64_SHARED = 1, PB_ROWSUM_FF_REGISTERS = 2,
+       PB_ROWSUM_FF_SHARED = 3 };
+pb_status pb_batch_set_tuning(int mode);
+pb_status pb_batch_force_shape(int rhs_width, int targets_per_thread, int row_sums, int ctas_per_sm);
+pb_status pb_batch_clear_tuning(void);
+int pb_batch_shapes(int rhs_width, int *targets_per_thread, int *row_sums, int max_out);
 
 /* Solve server with continuous batching (a library extension for serving;
  * the paper runs one molecule per run).  pb_server_create starts a worker

@@ -43,7 +43,9 @@ class _BatchInfo(ctypes.Structure):
                 ("iters_max", ctypes.c_int), ("iters_sum", ctypes.c_int64), ("rel_resid_max", ctypes.c_double),
                 ("rhs_width", ctypes.c_int), ("ctas", ctypes.c_int64), ("pair_evals", ctypes.c_int64),
                 ("pair_products", ctypes.c_int64), ("matvec_launches", ctypes.c_int64),
-                ("matvec_ms", ctypes.c_double)]
+                ("matvec_ms", ctypes.c_double), ("targets_per_thread", ctypes.c_int), ("row_sums", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("tuned", ctypes.c_int), ("tune_candidates", ctypes.c_int),
+                ("tune_ms", ctypes.c_double)]
 
 
 class _ServerOpts(ctypes.Structure):
@@ -101,7 +103,13 @@ SIGNATURES = {
     "pb_matvec_get_config": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64)]),
     "pb_matvec_autotune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "pb_matvec_configure_fp64": (_I, [_VP, _I, ctypes.POINTER(_I)]),
+    "pb_batch_set_tuning": (_I, [_I]),
+    "pb_batch_force_shape": (_I, [_I, _I, _I, _I]),
+    "pb_batch_clear_tuning": (_I, []),
+    "pb_batch_shapes": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), _I]),
 }
+
+ROW_SUMS = {0: "fp64-registers", 1: "fp64-shared", 2: "float-float-registers", 3: "float-float-shared"}
 
 _LIB = None
 
@@ -380,6 +388,29 @@ def pb_batch_solve(ctxs, charge_sets, restart: int = 10, tol: float = 1e-4, maxi
     d = {f: getattr(info, f) for f, _ in _BatchInfo._fields_}
     d["status"] = st
     return out, d
+
+
+def pb_batch_set_tuning(autotune: bool) -> None:
+    """Autotune the batched product per (width, size class) (default), or use the built-in shapes."""
+    _check(lib().pb_batch_set_tuning(1 if autotune else 0))
+
+
+def pb_batch_force_shape(rhs_width: int, targets_per_thread: int = 0, row_sums: int = 0,
+                         ctas_per_sm: int = 0) -> None:
+    """Force the batched product's shape for one width (targets_per_thread = 0 clears it)."""
+    _check(lib().pb_batch_force_shape(int(rhs_width), int(targets_per_thread), int(row_sums), int(ctas_per_sm)))
+
+
+def pb_batch_clear_tuning() -> None:
+    _check(lib().pb_batch_clear_tuning())
+
+
+def pb_batch_shapes(rhs_width: int) -> list:
+    """[(targets_per_thread, row_sums)] instantiated for a width, the default first."""
+    t = (ctypes.c_int * 16)()
+    r = (ctypes.c_int * 16)()
+    n = lib().pb_batch_shapes(int(rhs_width), t, r, 16)
+    return [(t[i], r[i]) for i in range(min(n, 16))]
 
 
 class Server:

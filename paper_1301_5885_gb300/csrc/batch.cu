@@ -22,8 +22,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
+#include "bmatvec.cuh"
 #include "engine.cuh"
 #include "fastmath.cuh"
 #include "pb_internal.cuh"
@@ -31,41 +36,10 @@
 
 namespace pb {
 
-constexpr int kBThreads = 128;          // product kernel threads
-constexpr int kBSourceTile = 256;       // sources per staged tile (one pair per thread)
-// targets per thread of the product kernel for R right-hand sides (more
-// targets share each staged source when fewer accumulators are needed)
-__host__ __device__ constexpr int bmatvec_targets(int R) { return R <= 1 ? 4 : 2; }
 constexpr int kChunk = 4096;            // vector chunk (elements) of the GMRES kernels
 constexpr int kVThreads = 256;
 constexpr int LDH = kMaxRestart + 1;
 
-struct BSurf {
-    const float4 *pos;
-    const float4 *nrm;
-    int64_t N;
-    float eps, inv_eps, kappa, nk;
-    double diag1, diag2;
-    int64_t tile_base;     // global index of this surface's first target tile
-    int64_t work_base;     // global index of its first (target tile, source tile) pair
-    int64_t S;             // source tiles
-    int inst0;             // first instance
-    int nrhs;
-};
-
-struct BInst {
-    double *b, *x, *w, *r, *V;   // V: (m+1) vectors of 2N
-    GmresState *st;
-    int64_t n2;
-    int surf;
-    int chunk0, nchunk;          // its chunks of the 2N vectors
-};
-
-struct BChunk {
-    int inst;
-    int len;
-    int64_t start;               // relative to the instance's vectors
-};
 
 namespace {
 
@@ -81,334 +55,6 @@ __device__ __forceinline__ bool inst_last(unsigned int *counter, unsigned int n)
     return s_last != 0;
 }
 
-// ---- the multi-surface, multi-right-hand-side product ------------------------
-__device__ __forceinline__ int find_surface(const BSurf *surf, int nsurf, int64_t p) {
-    int lo = 0, hi = nsurf - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (surf[mid].work_base <= p) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 p_dup(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-struct BConsts {
-    float2 nk2, mkap2, one2, mone2, three2, mthree2, meps2, epsm1, ieps2, omieps;
-};
-
-// K1..K4 of one target against one staged source pair (K0: only K2 and K3,
-// their constant factors being in the weights).
-template <bool K0>
-__device__ __forceinline__ void bcoef(const float4 &A, const float4 &Bq, const float4 &C, float2 x, float2 y,
-                                      float2 z, float2 nx, float2 ny, float2 nz, const BConsts &k, float2 &k1,
-                                      float2 &k2, float2 &k3, float2 &k4) {
-    const float2 dx = p_add(x, make_float2(A.x, A.y)), dy = p_add(y, make_float2(A.z, A.w));
-    const float2 dz = p_add(z, make_float2(Bq.x, Bq.y));
-    const float2 snx = make_float2(Bq.z, Bq.w), sny = make_float2(C.x, C.y), snz = make_float2(C.z, C.w);
-    const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
-    float2 inv, inv2;
-    // r^2 clamped below at 1e-18 for the MUFU; rho = r^2 (1/rho) uses the
-    // unclamped r^2, exactly 0 for a pair at zero distance
-    const float r2cx = fmaxf(r2.x, 1e-18f), r2cy = fmaxf(r2.y, 1e-18f);
-    inv.x = rsqrt_approx(r2cx);
-    inv.y = rsqrt_approx(r2cy);
-    if (K0) {
-        inv2 = p_mul(inv, inv);
-    } else {
-        inv2.x = rcp_approx(r2cx);
-        inv2.y = rcp_approx(r2cy);
-    }
-    const float2 inv3 = p_mul(inv2, inv);
-    const float2 ncx = p_fma(dx, nx, p_fma(dy, ny, p_mul(dz, nz)));   // -c_x
-    const float2 cy = p_fma(dx, snx, p_fma(dy, sny, p_mul(dz, snz)));
-    if (K0) {
-        k2 = p_mul(cy, inv3);
-        k3 = p_mul(ncx, inv3);
-    } else {
-        const float2 rho = p_mul(r2, inv);
-        const float2 arg = p_mul(k.nk2, rho);
-        float2 e;
-        e.x = exp2_approx(arg.x);
-        e.y = exp2_approx(arg.y);
-        const float2 mkr = p_mul(k.mkap2, rho);
-        const float2 nnn = p_fma(nx, snx, p_fma(ny, sny, p_mul(nz, snz)));   // -n
-        const float2 ome = p_fma(e, k.mone2, k.one2);
-        const float2 ome1 = p_fma(e, mkr, ome);                                // 1 - e (1 + kappa rho)
-        k1 = p_mul(ome, inv);
-        k2 = p_mul(p_mul(p_fma(ome1, k.meps2, k.epsm1), inv3), cy);
-        k3 = p_mul(p_mul(p_fma(ome1, k.ieps2, k.omieps), inv3), ncx);
-        const float2 p3 = p_fma(mkr, p_add(mkr, k.mthree2), k.three2);
-        const float2 e3 = p_fma(e, p3, k.mthree2);
-        const float2 ccy = p_mul(p_mul(e3, ncx), cy);
-        k4 = p_mul(p_fma(ccy, inv2, p_mul(ome1, nnn)), inv3);
-    }
-}
-
-// One staged source pair q against the thread's T targets, for the R
-// right-hand sides of the surface.
-template <int R, int T, bool K0>
-__device__ __forceinline__ void bstep(const float4 *s_g, const float4 *s_w, int q, const BConsts &k,
-                                      const float2 (&xi)[T], const float2 (&yi)[T], const float2 (&zi)[T],
-                                      const float2 (&nxi)[T], const float2 (&nyi)[T], const float2 (&nzi)[T],
-                                      float2 (&f1)[R][T], float2 (&f2)[R][T]) {
-    constexpr int TQ = kBSourceTile / 2;
-    float2 k1[T], k2[T], k3[T], k4[T];
-    const float4 A = s_g[q], Bq = s_g[TQ + q], C = s_g[2 * TQ + q];
-#pragma unroll
-    for (int t = 0; t < T; ++t)
-        bcoef<K0>(A, Bq, C, xi[t], yi[t], zi[t], nxi[t], nyi[t], nzi[t], k, k1[t], k2[t], k3[t], k4[t]);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const float4 w = s_w[r * TQ + q];
-        const float2 wpsi = make_float2(w.x, w.y), wphi = make_float2(w.z, w.w);
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            if (K0) {
-                f1[r][t] = p_fma(k2[t], wphi, f1[r][t]);
-                f2[r][t] = p_fma(k3[t], wpsi, f2[r][t]);
-            } else {
-                f1[r][t] = p_fma(k1[t], wpsi, p_fma(k2[t], wphi, f1[r][t]));
-                f2[r][t] = p_fma(k3[t], wpsi, p_fma(k4[t], wphi, f2[r][t]));
-            }
-        }
-    }
-}
-
-// One staged tile of source pairs against the thread's T targets, for the R
-// right-hand sides of the surface.  Packed f32x2: each instruction does a
-// step of two pairs (one target, two sources).  The target normals arrive
-// negated so that no operand needs a sign change: with c_x' = -c_x, n' = -n,
-// 1 - e' = 1 - e (1 + kappa rho) and -b (b the K3 factor),
-//   K1 = (1 - e)/rho,  K2 = a c_y,  K3 = (-b) c_x',
-//   K4 = (-e3 c_x c_y / rho^2 + (e' - 1) n) / rho^3 = ((e3 c_x' c_y) / rho^2 + (1 - e') n') / rho^3
-// with a = (eps e' - 1)/rho^3 and e3 = e (3 + 3 kappa rho + kappa^2 rho^2) - 3:
-// 36 FP32 operations per pair for K1..K4 and 4 per right-hand side.  With
-// kappa = 0 (K0), K1 = K4 = 0 and the constant factors of K2, K3 are folded
-// into the staged weights: 16 operations per pair and 2 per right-hand side.
-// The self pair is removed by the clamp of r^2 before the MUFU (every term
-// an exact zero, as in the single-surface kernels).
-template <int R, int T, bool K0>
-__device__ __forceinline__ void bstage(const float4 *s_g, const float4 *s_w, int npairs, float eps, float inv_eps,
-                                       float kappa, float nk, const float2 (&xi)[T], const float2 (&yi)[T],
-                                       const float2 (&zi)[T], const float2 (&nxi)[T], const float2 (&nyi)[T],
-                                       const float2 (&nzi)[T], float2 (&f1)[R][T], float2 (&f2)[R][T]) {
-    BConsts k;
-    k.nk2 = p_dup(nk);
-    k.mkap2 = p_dup(-kappa);
-    k.one2 = p_dup(1.f);
-    k.mone2 = p_dup(-1.f);
-    k.three2 = p_dup(3.f);
-    k.mthree2 = p_dup(-3.f);
-    k.meps2 = p_dup(-eps);
-    k.epsm1 = p_dup(eps - 1.f);
-    k.ieps2 = p_dup(inv_eps);
-    k.omieps = p_dup(1.f - inv_eps);
-#pragma unroll 1
-    for (int q = 0; q < npairs; ++q) bstep<R, T, K0>(s_g, s_w, q, k, xi, yi, zi, nxi, nyi, nzi, f1, f2);
-}
-
-// y_q = A u_q for every instance q; u_q = x_q (usel 0) or V_q[k] (usel 1), y_q = w_q.
-// CTA c owns the flattened (surface, target tile, source tile) range
-// [c W / G, (c+1) W / G); a target tile split over several CTAs is finished
-// by the last to arrive, which adds the partial rows in CTA order.
-template <int R>
-__global__ void __launch_bounds__(kBThreads)
-bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restrict__ inst, int64_t W, int64_t G,
-               int usel, int k, const int *__restrict__ active, double *__restrict__ partials,
-               unsigned int *__restrict__ counters, unsigned long long *__restrict__ evaluated) {
-    constexpr int BS = kBThreads, T = bmatvec_targets(R), TT = BS * T, TS = kBSourceTile, TQ = TS / 2;
-    static_assert(TQ == BS, "one source pair per thread when staging");
-    __shared__ float4 s_g[3 * TQ];       // {-x0,-x1,-y0,-y1}, {-z0,-z1,nx0,nx1}, {ny0,ny1,nz0,nz1}
-    __shared__ float4 s_w[R * TQ];       // per right-hand side {W dphi0, W dphi1, W phi0, W phi1} / (4 pi)
-    __shared__ const double *s_u[R];
-    __shared__ double *s_y[R];
-    __shared__ int s_last;
-    const int tid = threadIdx.x;
-    // FP64 row sums (rows of phi: w = 0, of dphi: w = 1): in registers, or in
-    // this thread's own shared-memory slots when there are many of them
-    constexpr bool SACC = R * T >= 16;
-    __shared__ double s_acc[SACC ? 2 * R * T * BS : 1];
-    double racc[SACC ? 1 : 2 * R * T];
-#define ACC(w, r, t) (SACC ? s_acc[(((w) * R + (r)) * T + (t)) * BS + tid] : racc[((w) * R + (r)) * T + (t)])
-    const int64_t c = blockIdx.x;
-    int64_t p = sk_begin(c, W, G);
-    const int64_t pend = sk_begin(c + 1, W, G);
-    // global target tile of this CTA's first pair (its partial slot 0)
-    int64_t first_tile = -1;
-    if (p < pend) {
-        const int s0 = find_surface(surf, nsurf, p);
-        first_tile = surf[s0].tile_base + (p - surf[s0].work_base) / surf[s0].S;
-    }
-
-    while (p < pend) {
-        const int si = find_surface(surf, nsurf, p);
-        const BSurf sf = surf[si];
-        const int64_t local = p - sf.work_base;
-        const int64_t S = sf.S;
-        const int64_t a = local / S;
-        const int64_t s_first = local % S;
-        const int64_t s_end = (S < s_first + (pend - p)) ? S : s_first + (pend - p);
-        const int64_t N = sf.N;
-        if (!vol(active + si)) {          // every instance of this surface is idle
-            p += s_end - s_first;
-            continue;
-        }
-        if (local == 0 && tid == 0) atomicAdd(evaluated + si, 1ull);   // one product of this surface
-        __syncthreads();                  // the previous segment is done with s_u / s_y
-        if (tid < R) {
-            if (tid < sf.nrhs) {
-                const BInst in = inst[sf.inst0 + tid];
-                s_u[tid] = usel ? in.V + (int64_t)k * in.n2 : in.x;
-                s_y[tid] = in.w;
-            } else {
-                s_u[tid] = nullptr;
-                s_y[tid] = nullptr;
-            }
-        }
-        const bool k0 = sf.kappa == 0.f;
-        // kappa = 0: (eps - 1) and (1/eps - 1) folded into the weights (K3 uses -c_x)
-        const float wphi_scale = k0 ? sf.eps - 1.f : 1.f, wpsi_scale = k0 ? 1.f - sf.inv_eps : 1.f;
-        float2 xi[T], yi[T], zi[T], nxi[T], nyi[T], nzi[T];
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            const int64_t i = a * TT + t * BS + tid;
-            const int64_t ic = i < N ? i : N - 1;
-            const float4 q = sf.pos[ic], n = sf.nrm[ic];
-            xi[t] = p_dup(q.x); yi[t] = p_dup(q.y); zi[t] = p_dup(q.z);
-            nxi[t] = p_dup(-n.x); nyi[t] = p_dup(-n.y); nzi[t] = p_dup(-n.z);
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int t = 0; t < T; ++t) { ACC(0, r, t) = 0.0; ACC(1, r, t) = 0.0; }
-
-        for (int64_t st = s_first; st < s_end; ++st) {
-            __syncthreads();
-            {
-                // stage source pair (2 tid, 2 tid + 1); a missing second source
-                // repeats the first with zero weights
-                const int64_t j0 = st * TS + 2 * tid;
-                if (j0 < N) {
-                    const bool has1 = j0 + 1 < N;
-                    const int64_t j1 = has1 ? j0 + 1 : j0;
-                    const float4 p0 = sf.pos[j0], p1 = sf.pos[j1], n0 = sf.nrm[j0], n1 = sf.nrm[j1];
-                    s_g[tid] = make_float4(-p0.x, -p1.x, -p0.y, -p1.y);
-                    s_g[TQ + tid] = make_float4(-p0.z, -p1.z, n0.x, n1.x);
-                    s_g[2 * TQ + tid] = make_float4(n0.y, n1.y, n0.z, n1.z);
-                    const float w0 = p0.w, w1 = has1 ? p1.w : 0.f;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const double *u = s_u[r];
-                        s_w[r * TQ + tid] = u ? make_float4((float)u[N + j0] * (w0 * wpsi_scale),
-                                                            (float)u[N + j1] * (w1 * wpsi_scale),
-                                                            (float)u[j0] * (w0 * wphi_scale),
-                                                            (float)u[j1] * (w1 * wphi_scale))
-                                              : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                }
-            }
-            __syncthreads();
-            const int64_t rem = N - st * TS;
-            const int npairs = (int)(((rem < TS) ? rem : TS) + 1) / 2;
-            float2 f1[R][T], f2[R][T];
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-#pragma unroll
-                for (int t = 0; t < T; ++t) { f1[r][t] = p_dup(0.f); f2[r][t] = p_dup(0.f); }
-            if (k0)
-                bstage<R, T, true>(s_g, s_w, npairs, sf.eps, sf.inv_eps, sf.kappa, sf.nk, xi, yi, zi, nxi, nyi, nzi,
-                                   f1, f2);
-            else
-                bstage<R, T, false>(s_g, s_w, npairs, sf.eps, sf.inv_eps, sf.kappa, sf.nk, xi, yi, zi, nxi, nyi, nzi,
-                                    f1, f2);
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-#pragma unroll
-                for (int t = 0; t < T; ++t) {
-                    ACC(0, r, t) += (double)f1[r][t].x + (double)f1[r][t].y;
-                    ACC(1, r, t) += (double)f2[r][t].x + (double)f2[r][t].y;
-                }
-        }
-
-        const int64_t p_tile0 = sf.work_base + a * S;
-        const int64_t c0 = sk_cta_of(p_tile0, W, G), c1 = sk_cta_of(p_tile0 + S - 1, W, G);
-        const int nseg = (int)(c1 - c0 + 1);
-        const int64_t gtile = sf.tile_base + a;
-        if (nseg == 1) {
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                const int64_t i = a * TT + t * BS + tid;
-                if (i < N) {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        if (s_y[r]) {
-                            s_y[r][i] = sf.diag1 * s_u[r][i] - ACC(0, r, t);
-                            s_y[r][N + i] = sf.diag2 * s_u[r][N + i] - ACC(1, r, t);
-                        }
-                    }
-                }
-            }
-        } else {
-            const int64_t slot = 2 * c + (gtile == first_tile ? 0 : 1);
-            double *mine = partials + slot * (2 * R * TT);
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-#pragma unroll
-                for (int t = 0; t < T; ++t) {
-                    mine[(2 * r) * TT + t * BS + tid] = ACC(0, r, t);
-                    mine[(2 * r + 1) * TT + t * BS + tid] = ACC(1, r, t);
-                }
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) s_last = (atomicAdd(&counters[gtile], 1u) == (unsigned int)(nseg - 1));
-            __syncthreads();
-            if (s_last) {
-                __threadfence();
-#pragma unroll
-                for (int t = 0; t < T; ++t) {
-                    double s1[R], s2[R];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) { s1[r] = 0.0; s2[r] = 0.0; }
-                    for (int o = 0; o < nseg; ++o) {
-                        const int64_t co = c0 + o;
-                        const int64_t pb0 = sk_begin(co, W, G);
-                        const int sc = find_surface(surf, nsurf, pb0);
-                        const int64_t ft = surf[sc].tile_base + (pb0 - surf[sc].work_base) / surf[sc].S;
-                        const double *pp = partials + (2 * co + (gtile == ft ? 0 : 1)) * (2 * R * TT);
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            s1[r] += __ldcg(pp + (2 * r) * TT + t * BS + tid);
-                            s2[r] += __ldcg(pp + (2 * r + 1) * TT + t * BS + tid);
-                        }
-                    }
-                    const int64_t i = a * TT + t * BS + tid;
-                    if (i < N) {
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            if (s_y[r]) {
-                                s_y[r][i] = sf.diag1 * s_u[r][i] - s1[r];
-                                s_y[r][N + i] = sf.diag2 * s_u[r][N + i] - s2[r];
-                            }
-                        }
-                    }
-                }
-                if (tid == 0) counters[gtile] = 0u;
-            }
-        }
-        p += s_end - s_first;
-    }
-}
-
-#undef ACC
 
 // ---- batched GMRES vector kernels (one block per chunk) ----------------------
 __global__ void __launch_bounds__(kVThreads)
@@ -783,18 +429,138 @@ void Engine::remove(EngineMember *mb) {
     dirty_ = true;
 }
 
+// ---------------------------------------------------------------------------
+// Batched-product tuning: process-wide mode, forced shapes and tuned choices
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+int g_tune_mode = 1;                                   // 0 built-in defaults, 1 autotune
+BmvConfig g_forced[kEngineMaxRhs + 1];                 // by width (T == 0: none)
+std::map<std::tuple<int, int, int64_t>, BmvConfig> g_tuned;   // (device, width, size class)
+
+double wall_seconds() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+BmvConfig default_config(int R) {
+    BmvShape sh[16];
+    bmatvec_shapes(R, sh, 16);
+    BmvConfig c;
+    c.T = sh[0].T;
+    c.acc = sh[0].acc;
+    c.ctas_per_sm = 0;
+    return c;
+}
+
+BmvArgs bmv_args(const BSurf *surf, int nsurf, const BInst *inst, int64_t W, int64_t G, int usel, int k,
+                 const int *act, double *part, unsigned int *cnt, unsigned long long *evals) {
+    BmvArgs a;
+    a.surf = surf;
+    a.nsurf = nsurf;
+    a.inst = inst;
+    a.W = W;
+    a.G = G;
+    a.usel = usel;
+    a.k = k;
+    a.active = act;
+    a.partials = part;
+    a.counters = cnt;
+    a.evaluated = evals;
+    return a;
+}
+}  // namespace
+
+void Engine::retile(std::vector<BSurf> &hs, const std::vector<char> &direct, int64_t TT, int64_t *tiles,
+                    int64_t *work) {
+    int64_t t = 0, w = 0;
+    for (size_t i = 0; i < hs.size(); ++i) {
+        const int64_t nt = direct[i] ? 0 : (hs[i].N + TT - 1) / TT;
+        hs[i].tile_base = t;
+        hs[i].work_base = w;
+        t += nt;
+        w += nt * hs[i].S;
+    }
+    *tiles = t;
+    *work = w;
+}
+
+// Times every instantiated shape of width R_ at every CTA count up to its
+// occupancy on the current work list (two launches each after one warm-up,
+// CUDA events on the engine's stream) and keeps the fastest.  The launches
+// read x and write w of the running instances, which the next cycle
+// recomputes first; the evaluation counters are cleared afterwards.
+pb_status Engine::tune(std::vector<BSurf> &hs, const std::vector<char> &direct, int64_t size_class) {
+    const double t0 = wall_seconds();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    BmvShape sh[16];
+    const int nsh = bmatvec_shapes(R_, sh, 16);
+    BmvConfig best = config;
+    float best_ms = 1e30f;
+    int tried = 0;
+    for (int i = 0; i < nsh && e == cudaSuccess; ++i) {
+        int occ = 0;
+        e = bmatvec_dispatch(R_, sh[i], BmvArgs{}, 0, stream_, &occ);
+        if (e != cudaSuccess) break;
+        if (occ < 1) continue;
+        int64_t tiles = 0, W = 0;
+        retile(hs, direct, (int64_t)kBThreads * sh[i].T, &tiles, &W);
+        if (W == 0) break;
+        e = cudaMemcpyAsync(d_surf_, hs.data(), hs.size() * sizeof(BSurf), cudaMemcpyHostToDevice, stream_);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+        for (int cps = 1; cps <= occ && e == cudaSuccess; ++cps) {
+            int64_t G = (int64_t)num_sms_ * cps;
+            if (G > W) G = W;
+            // every surface with a running instance takes part (the Arnoldi-step
+            // flags; the x-product flags are off for instances that start at x = 0)
+            const BmvArgs a = bmv_args(d_surf_, nsurf_, d_inst_, W, G, 0, 0, act_step_, part_, cnt_tile_, evals_);
+            e = bmatvec_dispatch(R_, sh[i], a, (unsigned)G, stream_, nullptr);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, stream_);
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) e = bmatvec_dispatch(R_, sh[i], a, (unsigned)G, stream_, nullptr);
+            count_launches(3);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, stream_);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            ++tried;
+            if (e == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                best.T = sh[i].T;
+                best.acc = sh[i].acc;
+                best.ctas_per_sm = cps;
+            }
+            if (G == W) break;               // more CTAs than work items change nothing
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "engine: tuning the batched product");
+    config = best;
+    tuned = true;
+    tune_candidates = tried;
+    tune_ms = 1e3 * (wall_seconds() - t0);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tuned[std::make_tuple(device_, R_, size_class)] = best;
+    }
+    return PB_OK;
+}
+
 pb_status Engine::rebuild() {
     std::vector<BSurf> hs;
     std::vector<BInst> hq;
     std::vector<BChunk> hch;
+    std::vector<char> direct_flag;
     surf_member_.clear();
     direct_.clear();
-    int64_t tiles = 0, work = 0;
+    tuned = false;
     int rmax = 1;
     for (EngineMember *mb : members_)
         if (!mb->finished && mb->nrhs > rmax) rmax = mb->nrhs;
     R_ = rmax <= 1 ? 1 : (rmax <= 2 ? 2 : (rmax <= 4 ? 4 : 8));
-    const int64_t TT = (int64_t)kBThreads * bmatvec_targets(R_);
+    double pairs = 0.0;      // pair evaluations of one batched launch (its size class)
     for (size_t mi = 0; mi < members_.size(); ++mi) {
         EngineMember *mb = members_[mi];
         if (mb->finished) continue;
@@ -813,15 +579,11 @@ pb_status Engine::rebuild() {
         // kernel: its own launch of that kernel (about 23 FP32 operations per
         // ordered pair against 40 in the batched kernel); no batched work
         const bool direct = mb->nrhs == 1 && f32_variant_symmetric(c->f32_variant);
-        const int64_t T = direct ? 0 : (c->N + TT - 1) / TT;
         sf.S = (c->N + kBSourceTile - 1) / kBSourceTile;
         if (direct) direct_.push_back((int)hs.size());
-        sf.tile_base = tiles;
-        sf.work_base = work;
+        else pairs += (double)c->N * (double)c->N;
         sf.inst0 = (int)hq.size();
         sf.nrhs = mb->nrhs;
-        tiles += T;
-        work += T * sf.S;
         const int64_t n2 = 2 * c->N;
         const size_t per = (size_t)(m_ + 5) * n2;
         for (int r = 0; r < mb->nrhs; ++r) {
@@ -842,13 +604,12 @@ pb_status Engine::rebuild() {
             hq.push_back(in);
         }
         hs.push_back(sf);
+        direct_flag.push_back(direct ? 1 : 0);
         surf_member_.push_back((int)mi);
     }
     nsurf_ = (int)hs.size();
     nq_ = (int)hq.size();
     nchunks_ = (int)hch.size();
-    tiles_ = tiles;
-    W_ = work;
     rhs_width = R_;
     if (gexec_) cudaGraphExecDestroy(gexec_);
     if (graph_) cudaGraphDestroy(graph_);
@@ -856,15 +617,70 @@ pb_status Engine::rebuild() {
     graph_ = nullptr;
     dirty_ = false;
     if (nsurf_ == 0) return PB_OK;
-    int occ = 0;
-    switch (R_) {
-        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bmatvec_kernel<1>, kBThreads, 0); break;
-        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bmatvec_kernel<2>, kBThreads, 0); break;
-        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bmatvec_kernel<4>, kBThreads, 0); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bmatvec_kernel<8>, kBThreads, 0); break;
+
+    // the product's shape: forced; the one this engine tuned or looked up
+    // first for this width (a batch keeps it as its members finish); tuned
+    // for this size class; tuned for the nearest size class within an
+    // octave; else the built-in default
+    const int64_t size_class = pairs > 1.0 ? (int64_t)floor(4.0 * log2(pairs)) : 0;
+    bool need_tune = false, forced = false;
+    config = default_config(R_);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        if (g_forced[R_].T > 0) {
+            config = g_forced[R_];
+            forced = true;
+        } else if (g_tune_mode == 1 && kept_R_ == R_) {
+            config = kept_;
+        } else if (g_tune_mode == 1) {
+            auto it = g_tuned.find(std::make_tuple(device_, R_, size_class));
+            if (it != g_tuned.end()) {
+                config = it->second;
+            } else if (autotune && pairs > 0.0) {
+                need_tune = true;
+            } else {
+                int64_t best_d = 5;
+                for (const auto &kv : g_tuned) {
+                    if (std::get<0>(kv.first) != device_ || std::get<1>(kv.first) != R_) continue;
+                    const int64_t d0 = std::get<2>(kv.first) - size_class, d = d0 < 0 ? -d0 : d0;
+                    if (d < best_d) {
+                        best_d = d;
+                        config = kv.second;
+                    }
+                }
+            }
+        }
     }
+    // buffer sizes cover every shape the tuner may try
+    int occ = 0;
+    cudaError_t qe = bmatvec_dispatch(R_, BmvShape{config.T, config.acc}, BmvArgs{}, 0, stream_, &occ);
+    if (qe != cudaSuccess) return cuda_fail(qe, "engine: batched product shape");
     if (occ < 1) occ = 1;
-    G_ = (int64_t)num_sms_ * occ;
+    size_t part_need = 0;
+    int64_t tiles_need = 0;
+    {
+        BmvShape sh[16];
+        const int nsh = need_tune ? bmatvec_shapes(R_, sh, 16) : 1;
+        if (!need_tune) sh[0] = BmvShape{config.T, config.acc};
+        for (int i = 0; i < nsh; ++i) {
+            int o = occ;
+            if (need_tune && bmatvec_dispatch(R_, sh[i], BmvArgs{}, 0, stream_, &o) != cudaSuccess) o = 1;
+            if (!need_tune && config.ctas_per_sm > 0 && config.ctas_per_sm < o) o = config.ctas_per_sm;
+            const int64_t TTi = (int64_t)kBThreads * sh[i].T;
+            const size_t need = (size_t)2 * num_sms_ * (o < 1 ? 1 : o) * 2 * R_ * TTi;
+            part_need = need > part_need ? need : part_need;
+            int64_t t = 0, w = 0;
+            retile(hs, direct_flag, TTi, &t, &w);
+            tiles_need = t > tiles_need ? t : tiles_need;
+        }
+    }
+    const int64_t TT = (int64_t)kBThreads * config.T;
+    int64_t tiles = 0, work = 0;
+    retile(hs, direct_flag, TT, &tiles, &work);
+    tiles_ = tiles;
+    W_ = work;
+    const int cps = (config.ctas_per_sm > 0 && config.ctas_per_sm < occ) ? config.ctas_per_sm : occ;
+    G_ = (int64_t)num_sms_ * cps;
     if (G_ > W_) G_ = W_;
     ctas = G_;
     for (int si : direct_) {
@@ -880,7 +696,7 @@ pb_status Engine::rebuild() {
     if (s == PB_OK) s = grow((void **)&d_inst_, &cap_inst_, nq_, sizeof(BInst), "engine instances");
     if (s == PB_OK) s = grow((void **)&d_ch_, &cap_ch_, nchunks_, sizeof(BChunk), "engine chunks");
     if (s == PB_OK) s = grow((void **)&cnt_inst_, &cap_cnt_inst_, nq_, sizeof(unsigned int), "engine counters");
-    if (s == PB_OK) s = grow((void **)&cnt_tile_, &cap_cnt_tile_, tiles_, sizeof(unsigned int), "engine counters");
+    if (s == PB_OK) s = grow((void **)&cnt_tile_, &cap_cnt_tile_, tiles_need, sizeof(unsigned int), "engine counters");
     if (s == PB_OK) s = grow((void **)&evals_, &cap_evals_, nsurf_, sizeof(unsigned long long), "engine counters");
     if (s == PB_OK) s = grow((void **)&act_step_, &cap_flags_, 2 * (size_t)nsurf_, sizeof(int), "engine flags");
     if (s == PB_OK) {
@@ -890,7 +706,7 @@ pb_status Engine::rebuild() {
         s = grow((void **)&act_ax_, &c2, cap_flags_, sizeof(int), "engine flags");
     }
     if (s == PB_OK) s = grow((void **)&red_, &cap_red_, (size_t)(m_ + 1) * nchunks_, sizeof(double), "engine reductions");
-    if (s == PB_OK) s = grow((void **)&part_, &cap_part_, (size_t)2 * G_ * 2 * R_ * TT, sizeof(double), "engine partials");
+    if (s == PB_OK) s = grow((void **)&part_, &cap_part_, part_need, sizeof(double), "engine partials");
     if (s == PB_OK && !scalar_) {
         cudaError_t e = pool_alloc((void **)&scalar_, 64 * sizeof(double), stream_);
         if (e != cudaSuccess) s = cuda_fail(e, "engine scalars");
@@ -916,7 +732,7 @@ pb_status Engine::rebuild() {
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_inst_, hq.data(), nq_ * sizeof(BInst), cudaMemcpyHostToDevice, stream_);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ch_, hch.data(), nchunks_ * sizeof(BChunk), cudaMemcpyHostToDevice, stream_);
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt_inst_, 0, nq_ * sizeof(unsigned int), stream_);
-    if (e == cudaSuccess) e = cudaMemsetAsync(cnt_tile_, 0, tiles_ * sizeof(unsigned int), stream_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt_tile_, 0, tiles_need * sizeof(unsigned int), stream_);
     if (e == cudaSuccess) e = cudaMemsetAsync(evals_, 0, nsurf_ * sizeof(unsigned long long), stream_);
     // the staging vectors are pageable and local: wait for the copies
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
@@ -926,7 +742,32 @@ pb_status Engine::rebuild() {
     bg_flags<<<(nsurf_ + 127) / 128, 128, 0, stream_>>>(d_surf_, nsurf_, d_inst_, act_step_, act_ax_, 0);
     count_launch();
     e = cudaGetLastError();
-    return e == cudaSuccess ? PB_OK : cuda_fail(e, "engine flags");
+    if (e != cudaSuccess) return cuda_fail(e, "engine flags");
+    if (!need_tune) {
+        if (autotune && !forced) {
+            kept_ = config;
+            kept_R_ = R_;
+        }
+        return PB_OK;
+    }
+
+    // tune on this work list, then install the choice
+    if ((s = tune(hs, direct_flag, size_class)) != PB_OK) return s;
+    kept_ = config;
+    kept_R_ = R_;
+    retile(hs, direct_flag, (int64_t)kBThreads * config.T, &tiles, &work);
+    tiles_ = tiles;
+    W_ = work;
+    occ = 1;
+    e = bmatvec_dispatch(R_, BmvShape{config.T, config.acc}, BmvArgs{}, 0, stream_, &occ);
+    if (e != cudaSuccess) return cuda_fail(e, "engine: batched product shape");
+    G_ = (int64_t)num_sms_ * ((config.ctas_per_sm > 0 && config.ctas_per_sm < occ) ? config.ctas_per_sm : occ);
+    if (G_ > W_) G_ = W_;
+    ctas = G_;
+    e = cudaMemcpyAsync(d_surf_, hs.data(), nsurf_ * sizeof(BSurf), cudaMemcpyHostToDevice, stream_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(evals_, 0, nsurf_ * sizeof(unsigned long long), stream_);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    return e == cudaSuccess ? PB_OK : cuda_fail(e, "engine table upload");
 }
 
 void Engine::enqueue_cycle() {
@@ -934,12 +775,9 @@ void Engine::enqueue_cycle() {
     auto mv = [&](int usel, int k, const int *act) {
         if (timing_ && ev_used_ + 2 <= (int)ev_.size()) cudaEventRecord(ev_[ev_used_], stream_);
         if (W_ > 0) {
-            switch (R_) {
-                case 1: bmatvec_kernel<1><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
-                case 2: bmatvec_kernel<2><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
-                case 4: bmatvec_kernel<4><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
-                default: bmatvec_kernel<8><<<(unsigned)G_, kBThreads, 0, stream_>>>(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_); break;
-            }
+            bmatvec_dispatch(R_, BmvShape{config.T, config.acc},
+                             bmv_args(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_),
+                             (unsigned)G_, stream_, nullptr);
             ++cycle_kernels_;
             ++cycle_mv_;
         }
@@ -1124,13 +962,22 @@ extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double
             return set_error(lead, PB_ERR_ARG, "pb_batch_solve: bad charges for surface %d", s);
     }
     Engine eng(lead->stream, lead->device, lead->num_sms, o.restart, o.tol, o.maxit);
+    eng.autotune = true;
     std::vector<EngineMember *> mem(nsurf, nullptr);
     pb_status s = PB_OK;
     for (int i = 0; i < nsurf && s == PB_OK; ++i) mem[i] = eng.add(ctxs[i], charges[i], nc[i], nrhs[i], (uint64_t)i, &s);
     if (s != PB_OK) return set_error(lead, s, "%s", eng.error);
     bool all = false;
+    int tuned_any = 0, tune_candidates = 0;
+    double tune_ms = 0.0;
     for (int cyc = 0; cyc < o.maxit + 2 && s == PB_OK && !all; ++cyc) {
         s = eng.cycle(use_graph == 1, use_graph == 2);
+        if (eng.tuned) {
+            tuned_any = 1;
+            tune_candidates += eng.tune_candidates;
+            tune_ms += eng.tune_ms;
+            eng.tuned = false;
+        }
         all = true;
         for (EngineMember *mb : mem) all &= mb->finished;
     }
@@ -1167,8 +1014,60 @@ extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double
         info->pair_products = eng.pair_products;
         info->matvec_launches = eng.matvec_launches;
         info->matvec_ms = eng.matvec_ms;
+        info->targets_per_thread = eng.config.T;
+        info->row_sums = eng.config.acc;
+        info->ctas_per_sm = eng.config.ctas_per_sm;
+        info->tuned = tuned_any;
+        info->tune_candidates = tune_candidates;
+        info->tune_ms = tune_ms;
     }
     if (worst != PB_OK)
         return set_error(lead, worst, "pb_batch_solve: %d of %d instances did not converge", nq - nconv, nq);
     return PB_OK;
+}
+
+extern "C" pb_status pb_batch_set_tuning(int mode) {
+    if (mode != 0 && mode != 1) return set_error(nullptr, PB_ERR_ARG, "pb_batch_set_tuning: mode must be 0 or 1");
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_mode = mode;
+    return PB_OK;
+}
+
+extern "C" pb_status pb_batch_force_shape(int rhs_width, int targets_per_thread, int row_sums, int ctas_per_sm) {
+    if (rhs_width != 1 && rhs_width != 2 && rhs_width != 4 && rhs_width != 8)
+        return set_error(nullptr, PB_ERR_ARG, "pb_batch_force_shape: width must be 1, 2, 4 or 8");
+    if (ctas_per_sm < 0) return set_error(nullptr, PB_ERR_ARG, "pb_batch_force_shape: ctas_per_sm < 0");
+    BmvConfig c;
+    if (targets_per_thread > 0) {
+        BmvShape sh[16];
+        const int n = bmatvec_shapes(rhs_width, sh, 16);
+        bool found = false;
+        for (int i = 0; i < n; ++i) found |= sh[i].T == targets_per_thread && sh[i].acc == row_sums;
+        if (!found)
+            return set_error(nullptr, PB_ERR_ARG,
+                             "pb_batch_force_shape: (targets %d, row sums %d) is not a shape of width %d",
+                             targets_per_thread, row_sums, rhs_width);
+        c.T = targets_per_thread;
+        c.acc = row_sums;
+        c.ctas_per_sm = ctas_per_sm;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_forced[rhs_width] = c;
+    return PB_OK;
+}
+
+extern "C" pb_status pb_batch_clear_tuning(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned.clear();
+    return PB_OK;
+}
+
+extern "C" int pb_batch_shapes(int rhs_width, int *targets_per_thread, int *row_sums, int max_out) {
+    BmvShape sh[16];
+    const int n = bmatvec_shapes(rhs_width, sh, 16);
+    for (int i = 0; i < n && i < max_out; ++i) {
+        if (targets_per_thread) targets_per_thread[i] = sh[i].T;
+        if (row_sums) row_sums[i] = sh[i].acc;
+    }
+    return n;
 }

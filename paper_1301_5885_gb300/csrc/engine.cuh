@@ -18,6 +18,14 @@ struct BSurf;
 struct BInst;
 struct BChunk;
 
+// Shape and grid of the batched product (bmatvec.cuh): targets per thread,
+// placement and arithmetic of the row sums, CTAs per SM (0: the occupancy).
+struct BmvConfig {
+    int T = 0;
+    int acc = 0;
+    int ctas_per_sm = 0;
+};
+
 struct BStatus {
     int done, converged, status, iters, cycles, pad;
     double rel_resid;
@@ -66,10 +74,21 @@ class Engine {
     int cycles_run = 0;
     int rhs_width = 1;
     int64_t ctas = 0;
+    // batched-product shape: with autotune, a batch whose (width, size class)
+    // has no cached choice is tuned when its tables are built (every shape at
+    // every CTA count, timed on the batch's own work list); otherwise the
+    // cached choice of the nearest size class, else the built-in default
+    bool autotune = false;
+    BmvConfig config;
+    bool tuned = false;           // the last rebuild ran the tuner
+    int tune_candidates = 0;
+    double tune_ms = 0.0;         // host time spent tuning
     char error[512] = {0};
 
   private:
     pb_status rebuild();
+    pb_status tune(std::vector<BSurf> &hs, const std::vector<char> &direct, int64_t size_class);
+    void retile(std::vector<BSurf> &hs, const std::vector<char> &direct, int64_t TT, int64_t *tiles, int64_t *work);
     pb_status grow(void **p, size_t *cap, size_t need, size_t elem, const char *what);
     void enqueue_cycle();
     pb_status fail(pb_status s, const char *fmt, ...);
@@ -100,6 +119,8 @@ class Engine {
     cudaGraph_t graph_ = nullptr;
     int kernels_per_cycle_ = 0, mv_per_cycle_ = 0, cycle_kernels_ = 0, cycle_mv_ = 0;
     bool timing_ = false;
+    BmvConfig kept_;             // an autotuning engine's choice, kept across rebuilds
+    int kept_R_ = 0;
     std::vector<cudaEvent_t> ev_;
     int ev_used_ = 0;
 };

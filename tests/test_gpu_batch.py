@@ -106,3 +106,77 @@ def test_batch_rejects_bad_arguments():
     with pb.pb_create(p.surface.centroids, p.surface.normals, p.surface.areas, p.charges, 1.0, 80.0, 0.1) as ctx:
         with pytest.raises(pb.PBError):
             pb.pb_batch_solve([ctx], [np.repeat(p.charges[None], 9, axis=0)])   # more than 8 charge sets
+
+
+def _small_mix():
+    """A batch small enough to tune quickly: widths 8 (the widest set) with
+    uneven surfaces, kappa in {0, 0.1257}, no direct surfaces."""
+    out = []
+    for k, (lvl, rad, nq, nr, kap) in enumerate([(3, 5.0, 6, 8, 0.1257), (4, 8.0, 10, 5, 0.0),
+                                                (3, 6.0, 5, 3, 0.1257), (2, 3.0, 3, 1, 0.1257)]):
+        p = pi.kirkwood_sphere_multi(level=lvl, radius=rad, n_charges=nq, seed=80 + k, kappa=kap)
+        out.append((p, pi.charge_variants(p.charges, nr, seed=90 + k, frac=0.3)))
+    return out
+
+
+def _solve_mix(mix, **kw):
+    pb = _pb()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctxs = [pb.pb_create(p.surface.centroids, p.surface.normals, p.surface.areas, sets[0], p.eps1, p.eps2,
+                             p.kappa, stream=stream) for p, sets in mix]
+        try:
+            return pb.pb_batch_solve(ctxs, [sets for _, sets in mix], tol=1e-7, maxit=2000, **kw)
+        finally:
+            for c in ctxs:
+                pb.pb_destroy(c)
+
+
+@pytest.mark.parametrize("width", [1, 2, 4, 8])
+def test_every_batched_product_shape_gives_the_same_energies(width):
+    """Each instantiated shape (targets per thread, FP64 or float-float row
+    sums in registers or shared memory) and CTA count computes the same
+    products: energies within 2e-6 of the built-in default shape."""
+    pb = _pb()
+    mix = [(p, sets[:width]) for p, sets in _small_mix()]
+    mix[0] = (mix[0][0], pi.charge_variants(mix[0][0].charges, width, seed=95, frac=0.3))
+    pb.pb_batch_set_tuning(False)
+    try:
+        ref, info = _solve_mix(mix)
+        assert info["rhs_width"] == width and info["tuned"] == 0
+        for t, r in pb.pb_batch_shapes(width):
+            for cps in (1, 0):
+                pb.pb_batch_force_shape(width, t, r, cps)
+                got, gi = _solve_mix(mix, use_graph=(cps == 0))
+                assert (gi["targets_per_thread"], gi["row_sums"], gi["ctas_per_sm"]) == (t, r, cps)
+                for a, b in zip(got, ref):
+                    assert a == pytest.approx(b, rel=2e-6, abs=1e-9), (t, r, cps)
+    finally:
+        pb.pb_batch_force_shape(width)
+        pb.pb_batch_set_tuning(True)
+
+
+def test_autotuned_batch_matches_the_default_and_the_oracle():
+    """The autotuner times every shape on the batch's own work list, caches
+    the choice, and the tuned run gives the default run's energies to 2e-6
+    and the oracle's to 1e-5; a second batch of the same size class reuses the
+    cached choice without tuning."""
+    pb = _pb()
+    mix = _small_mix()
+    pb.pb_batch_set_tuning(False)
+    ref, _ = _solve_mix(mix)
+    pb.pb_batch_set_tuning(True)
+    pb.pb_batch_clear_tuning()
+    got, info = _solve_mix(mix)
+    assert info["tuned"] == 1 and info["tune_candidates"] >= len(pb.pb_batch_shapes(8))
+    assert (info["targets_per_thread"], info["row_sums"]) in pb.pb_batch_shapes(8)
+    for a, b in zip(got, ref):
+        assert a == pytest.approx(b, rel=2e-6, abs=1e-9)
+    again, info2 = _solve_mix(mix)
+    assert info2["tuned"] == 0
+    assert (info2["targets_per_thread"], info2["row_sums"], info2["ctas_per_sm"]) == \
+        (info["targets_per_thread"], info["row_sums"], info["ctas_per_sm"])
+    for (p, sets), es in zip(mix[:1], got[:1]):
+        for r, q in enumerate(sets):
+            e = oracle.solve(p.surface, q, p.eps1, p.eps2, p.kappa, tol=1e-11)["energy"]
+            assert es[r] == pytest.approx(e, rel=1e-5)

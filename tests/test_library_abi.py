@@ -76,3 +76,21 @@ def test_python_binding_raises_without_cpu_fallback(lib):
     with pytest.raises(pb.PBError) as ei:
         pb.pb_create(np.zeros((1, 3)), np.zeros((1, 3)), np.ones(1), None, 1.0, -80.0, 0.0)
     assert ei.value.status == pb.PB_ERR_ARG
+
+
+def test_batched_product_shapes_and_overrides_are_checked_on_the_host(lib):
+    for width in (1, 2, 4, 8):
+        shapes = pb.pb_batch_shapes(width)
+        assert len(shapes) >= 4 and len(set(shapes)) == len(shapes)
+        assert all(t in (1, 2, 4) and r in pb._ffi.ROW_SUMS for t, r in shapes)
+    assert pb.pb_batch_shapes(3) == []
+    with pytest.raises(pb.PBError):
+        pb.pb_batch_force_shape(3, 2, 0)
+    with pytest.raises(pb.PBError):
+        pb.pb_batch_force_shape(8, 4, 0)            # not instantiated
+    t, r = pb.pb_batch_shapes(8)[1]
+    pb.pb_batch_force_shape(8, t, r, 2)
+    pb.pb_batch_force_shape(8)                      # cleared
+    assert lib.pb_batch_set_tuning(2) == pb.PB_ERR_ARG
+    pb.pb_batch_set_tuning(True)
+    pb.pb_batch_clear_tuning()
