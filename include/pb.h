@@ -342,6 +342,46 @@ pb_status pb_matvec_autotune(pb_ctx *ctx, int reps, int *variant, int *ctas_per_
  * variant now in use. */
 pb_status pb_matvec_configure_fp64(pb_ctx *ctx, int variant, int *variant_out);
 
+/* Row-block product: rows [row0, row0 + nrows) of both row blocks of
+ * Eqs. (12)-(13), y_rows[t] = (A u)_{row0 + t} and y_rows[nrows + t] =
+ * (A u)_{N + row0 + t} for t < nrows.  u: device, 2N FP64 (all of it is
+ * read); y_rows: device, 2 nrows FP64, caller-owned, must not overlap u.
+ * prec: PB_FP32PAIR (the packed stream-K kernel) or PB_FP64 (the plain FP64
+ * kernel); PB_ERR_ARG for PB_FLOAT2 or rows outside [0, N).  The same sums
+ * as the plain full product restricted to those rows (the symmetric
+ * variants have no row-block form).  Scratch grows on first use. */
+pb_status pb_matvec_rows(pb_ctx *ctx, const double *u, double *y_rows, int64_t row0, int64_t nrows,
+                         pb_precision prec);
+
+/* Row-sharded solve over `world` ranks, one GPU each (a library extension;
+ * the paper names multiple GPUs as future work, Section 4).  Rank p owns
+ * rows [p P, p P + n_p), P = ceil(N / world) (pb_shard_rows).  Every rank
+ * creates its own context with the whole surface and the same charges and
+ * calls pb_solve_sharded with the same options; GMRES, the source term and
+ * the energy run replicated, and each product of A evaluates only the rank's
+ * rows, then calls
+ *     allgather(user, send, recv, count, cuda_stream)
+ * with send: device, count = 2P doubles (the rank's phi rows in the first P
+ * slots, its psi rows in the next P; unused slots zero) and recv: device,
+ * world x count doubles to be filled in rank order; the callback must enqueue
+ * the collective so that it is ordered after the work already on cuda_stream
+ * and before work enqueued after it returns (NCCL on that stream does this),
+ * and return 0 on success (anything else ends the solve with PB_ERR_CUDA).
+ * It is called from the calling thread, once per product.  The gathered rows
+ * are unpacked into the full 2N vector on every rank, so every rank holds the
+ * same x, info and energy.  Options, x0, x_out, info and errors as for
+ * pb_solve; PB_FP32PAIR or PB_FP64 products only (PB_ERR_ARG for PB_FLOAT2,
+ * including as the refinement precision). */
+typedef int (*pb_allgather_fn)(void *user, const double *send, double *recv, int64_t count, void *cuda_stream);
+pb_status pb_solve_sharded(pb_ctx *ctx, const pb_solve_opts *opts, int rank, int world, pb_allgather_fn allgather,
+                           void *user, const double *x0, double *x_out, pb_solve_info *info);
+
+/* Host helpers of the sharded layout (no GPU needed): the rows of a rank,
+ * and the unpacking of a gathered buffer (world blocks of 2P doubles, as
+ * above) into the 2N vector [phi; psi]. */
+pb_status pb_shard_rows(int64_t N, int world, int rank, int64_t *row0, int64_t *nrows, int64_t *rows_per_rank);
+pb_status pb_shard_unpack_host(const double *gathered, int64_t N, int world, double *y);
+
 /* No-allocation matrix-vector product.  The paper has no counterpart: this is
  * a library convenience for callers that cannot call cudaMalloc (for example
  * code running under a framework whose caching allocator already owns all of

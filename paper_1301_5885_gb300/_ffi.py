@@ -103,6 +103,10 @@ SIGNATURES = {
     "pb_matvec_get_config": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64)]),
     "pb_matvec_autotune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "pb_matvec_configure_fp64": (_I, [_VP, _I, ctypes.POINTER(_I)]),
+    "pb_matvec_rows": (_I, [_VP, _VP, _VP, _I64, _I64, _I]),
+    "pb_solve_sharded": (_I, [_VP, ctypes.POINTER(_Opts), _I, _I, _VP, _VP, _VP, _VP, ctypes.POINTER(_Info)]),
+    "pb_shard_rows": (_I, [_I64, _I, _I, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "pb_shard_unpack_host": (_I, [_VP, _I64, _I, _VP]),
     "pb_batch_set_tuning": (_I, [_I]),
     "pb_batch_force_shape": (_I, [_I, _I, _I, _I]),
     "pb_batch_clear_tuning": (_I, []),
@@ -208,10 +212,11 @@ def _stream_ptr(stream):
 class Context:
     """An owned pb_ctx handle."""
 
-    def __init__(self, handle, n: int, nc: int):
+    def __init__(self, handle, n: int, nc: int, stream=None):
         self.handle = handle
         self.n = n
         self.nc = nc
+        self.stream = stream
 
     def __enter__(self):
         return self
@@ -249,7 +254,7 @@ def pb_create(centroids, normals, areas, charges, eps1: float, eps2: float, kapp
                          _ptr_f64(q, 4 * nc, "charges", keep) if nc > 0 else None, nc,
                          float(eps1), float(eps2), float(kappa), _stream_ptr(stream), ctypes.byref(out))
     _check(st)
-    return Context(out.value, n, nc)
+    return Context(out.value, n, nc, stream)
 
 
 def pb_set_charges(ctx: Context, charges) -> None:
@@ -276,6 +281,96 @@ def pb_solve(ctx: Context, restart: int = 10, tol: float = 1e-4, maxit: int = 10
     x0p = _device_vec(x0, 2 * ctx.n, "x0") if x0 is not None else None
     xop = _device_vec(x_out, 2 * ctx.n, "x_out") if x_out is not None else None
     st = lib().pb_solve(ctx.handle, ctypes.byref(o), x0p, xop, ctypes.byref(info))
+    if st != PB_OK and not (st == PB_ERR_NOCONV and not raise_on_noconv):
+        _check(st, ctx)
+    return SolveInfo(st, info.iters, info.cycles, info.rel_resid, info.energy_kcal, info.rel_resid_fp64,
+                     info.refine_steps, info.matvecs)
+
+
+def pb_matvec_rows(ctx: Context, u, y_rows, row0: int, nrows: int, prec="fp32pair") -> None:
+    """Rows [row0, row0 + nrows) of both row blocks of A u into y_rows (2 nrows:
+    phi rows, then psi rows); u is the full 2N device vector."""
+    _check(lib().pb_matvec_rows(ctx.handle, _device_vec(u, 2 * ctx.n, "u"), _device_vec(y_rows, 2 * int(nrows), "y"),
+                                int(row0), int(nrows), PRECISIONS[prec]), ctx)
+
+
+def pb_shard_rows(n: int, world: int, rank: int):
+    """(row0, nrows, rows_per_rank) of a rank in the row-sharded layout."""
+    r0, nr, per = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().pb_shard_rows(int(n), int(world), int(rank), ctypes.byref(r0), ctypes.byref(nr), ctypes.byref(per)))
+    return r0.value, nr.value, per.value
+
+
+def pb_shard_unpack_host(gathered, n: int, world: int) -> np.ndarray:
+    """The 2N vector [phi; psi] from a gathered host buffer of world blocks of
+    2 P doubles (each rank's phi rows, then its psi rows, P slots each)."""
+    g = np.ascontiguousarray(np.asarray(gathered, dtype=np.float64))
+    per = (int(n) + int(world) - 1) // int(world)
+    if g.size != 2 * per * int(world):
+        raise ValueError(f"gathered buffer has {g.size} doubles, expected {2 * per * int(world)}")
+    y = np.empty(2 * int(n))
+    _check(lib().pb_shard_unpack_host(g.ctypes.data, int(n), int(world), y.ctypes.data))
+    return y
+
+
+class _DeviceArray:
+    """A raw FP64 device array seen through __cuda_array_interface__, so that
+    torch can wrap library-owned memory without a copy."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
+_GATHER_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                              ctypes.c_void_p)
+
+
+def pb_solve_sharded(ctx: Context, group=None, restart: int = 10, tol: float = 1e-4, maxit: int = 1000,
+                     prec="fp32pair", refine: int = 0, x0=None, x_out=None, raise_on_noconv: bool = True,
+                     refine_prec="fp64", allgather=None) -> SolveInfo:
+    """Row-sharded solve: this process is one rank of ``group`` (a
+    torch.distributed process group, the default group if None), each rank on
+    its own GPU with its own context of the whole surface.  Every product
+    evaluates this rank's rows and gathers all ranks' rows with
+    torch.distributed.all_gather_into_tensor on the context's stream.
+    ``allgather(send, recv, count)``, if given, replaces the collective (it
+    receives torch views of the library's buffers)."""
+    import torch
+    import torch.distributed as dist
+    if allgather is None:
+        world, rank = dist.get_world_size(group), dist.get_rank(group)
+    else:
+        world, rank = 1, 0
+    stream = ctx.stream
+    if stream is not None and not isinstance(stream, torch.cuda.Stream):
+        stream = torch.cuda.ExternalStream(_stream_ptr(stream))
+    errors = []
+
+    def _gather(user, send, recv, count, cuda_stream):
+        try:
+            s = torch.as_tensor(_DeviceArray(send, count), device="cuda")
+            r = torch.as_tensor(_DeviceArray(recv, count * world), device="cuda")
+            st = stream if stream is not None else torch.cuda.default_stream()
+            with torch.cuda.stream(st):
+                if allgather is not None:
+                    allgather(s, r, int(count))
+                else:
+                    dist.all_gather_into_tensor(r, s, group=group)
+            return 0
+        except Exception as e:          # reported through the status code
+            errors.append(e)
+            return 1
+
+    cb = _GATHER_FN(_gather)
+    o = _Opts(int(restart), float(tol), int(maxit), PRECISIONS[prec], int(refine), PRECISIONS[refine_prec])
+    info = _Info()
+    x0p = _device_vec(x0, 2 * ctx.n, "x0") if x0 is not None else None
+    xop = _device_vec(x_out, 2 * ctx.n, "x_out") if x_out is not None else None
+    st = lib().pb_solve_sharded(ctx.handle, ctypes.byref(o), int(rank), int(world), ctypes.cast(cb, ctypes.c_void_p),
+                                None, x0p, xop, ctypes.byref(info))
+    if errors:
+        raise errors[0]
     if st != PB_OK and not (st == PB_ERR_NOCONV and not raise_on_noconv):
         _check(st, ctx)
     return SolveInfo(st, info.iters, info.cycles, info.rel_resid, info.energy_kcal, info.rel_resid_fp64,

@@ -11,12 +11,18 @@ namespace pb {
 
 // Finish a segment: either write y directly (one CTA covers the whole target
 // tile) or publish partial rows and let the last arriving CTA reduce them.
+// Target row t of the segment is row rb.row0 + t of both blocks of A u; it
+// is written to y[t] (phi block) and y[rb.ld + t] (psi block), so the full
+// product (rb = {0, N, N}) writes y[i] and y[N + i].
 template <int TT, int T, int BS>
 __device__ __forceinline__ void finish_segment(const StreamKPlan &plan, int64_t a, int64_t c,
                                                const double (&acc1)[T], const double (&acc2)[T],
-                                               const double *__restrict__ u, int64_t N, double diag1,
+                                               const double *__restrict__ u, int64_t N, RowBlock rb, double diag1,
                                                double diag2, double *__restrict__ partials,
                                                unsigned int *__restrict__ counters, double *__restrict__ y) {
+    const double *__restrict__ uphi = u + rb.row0;
+    const double *__restrict__ upsi = u + N + rb.row0;
+    double *__restrict__ ypsi = y + rb.ld;
     const int64_t S = plan.source_tiles;
     const int64_t c0 = sk_cta_of(a * S, plan.work, plan.ctas);
     const int64_t c1 = sk_cta_of(a * S + S - 1, plan.work, plan.ctas);
@@ -26,9 +32,9 @@ __device__ __forceinline__ void finish_segment(const StreamKPlan &plan, int64_t 
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             int64_t i = a * TT + t * BS + tid;
-            if (i < N) {
-                y[i] = diag1 * u[i] - acc1[t];
-                y[N + i] = diag2 * u[N + i] - acc2[t];
+            if (i < rb.nrows) {
+                y[i] = diag1 * uphi[i] - acc1[t];
+                ypsi[i] = diag2 * upsi[i] - acc2[t];
             }
         }
         return;
@@ -59,9 +65,9 @@ __device__ __forceinline__ void finish_segment(const StreamKPlan &plan, int64_t 
             s1 += __ldcg(pp + t * BS + tid);
             s2 += __ldcg(pp + TT + t * BS + tid);
         }
-        if (i < N) {
-            y[i] = diag1 * u[i] - s1;
-            y[N + i] = diag2 * u[N + i] - s2;
+        if (i < rb.nrows) {
+            y[i] = diag1 * uphi[i] - s1;
+            ypsi[i] = diag2 * upsi[i] - s2;
         }
     }
     if (tid == 0) counters[a] = 0u;   // ready for the next launch

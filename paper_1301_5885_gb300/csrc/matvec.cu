@@ -32,9 +32,14 @@
 namespace pb {
 
 StreamKPlan make_plan(int64_t n, int target_tile, int source_tile, int64_t ctas_wanted) {
+    return make_plan_rows(n, n, target_tile, source_tile, ctas_wanted);
+}
+
+StreamKPlan make_plan_rows(int64_t n_targets, int64_t n_sources, int target_tile, int source_tile,
+                           int64_t ctas_wanted) {
     StreamKPlan p;
-    p.target_tiles = (n + target_tile - 1) / target_tile;
-    p.source_tiles = (n + source_tile - 1) / source_tile;
+    p.target_tiles = (n_targets + target_tile - 1) / target_tile;
+    p.source_tiles = (n_sources + source_tile - 1) / source_tile;
     p.work = p.target_tiles * p.source_tiles;
     p.ctas = ctas_wanted < 1 ? 1 : (ctas_wanted > p.work ? p.work : ctas_wanted);
     p.max_segments = 1;
@@ -163,7 +168,8 @@ matvec_f32_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
 #pragma unroll
             for (int t = 0; t < T; ++t) { acc1[t] += (double)f1[t]; acc2[t] += (double)f2[t]; }
         }
-        finish_segment<TT, T, BS>(plan, a, c, acc1, acc2, u, N, prm.diag1, prm.diag2, partials, counters, y);
+        finish_segment<TT, T, BS>(plan, a, c, acc1, acc2, u, N, RowBlock{0, N, N}, prm.diag1, prm.diag2, partials,
+                                  counters, y);
         p += s_end - s_first;
     }
 }
@@ -213,7 +219,7 @@ constexpr float kRho2Min = 1e-18f;
 template <int T, bool K0>
 __global__ void __launch_bounds__(kF32Threads)
 matvec_f32x2_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm,
-                    const double *__restrict__ u, int64_t N, F32Params prm, StreamKPlan plan,
+                    const double *__restrict__ u, int64_t N, RowBlock rb, F32Params prm, StreamKPlan plan,
                     double *__restrict__ partials, unsigned int *__restrict__ counters,
                     double *__restrict__ y, const int *__restrict__ skip, unsigned long long *__restrict__ evaluated) {
     constexpr int BS = kF32Threads, TT = BS * T, TS = kF32SourceTile, TQ = TS / 2;
@@ -242,8 +248,8 @@ matvec_f32x2_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ n
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             int64_t i = a * TT + t * BS + tid;
-            if (i > N - 1) i = N - 1;
-            const float4 q = pos[i], n = nrm[i];
+            if (i > rb.nrows - 1) i = rb.nrows - 1;
+            const float4 q = pos[rb.row0 + i], n = nrm[rb.row0 + i];
             xi[t] = p_dup(q.x); yi[t] = p_dup(q.y); zi[t] = p_dup(q.z);
             nxi[t] = p_dup(n.x); nyi[t] = p_dup(n.y); nzi[t] = p_dup(n.z);
         }
@@ -328,7 +334,7 @@ matvec_f32x2_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ n
                 acc2[t] += (double)f2[t].x + (double)f2[t].y;
             }
         }
-        finish_segment<TT, T, BS>(plan, a, c, acc1, acc2, u, N, prm.diag1, prm.diag2, partials, counters, y);
+        finish_segment<TT, T, BS>(plan, a, c, acc1, acc2, u, N, rb, prm.diag1, prm.diag2, partials, counters, y);
         p += s_end - s_first;
     }
 }
@@ -626,8 +632,8 @@ struct F64Params {
 };
 
 __global__ void __launch_bounds__(kF64Threads)
-matvec_f64_kernel(const double *__restrict__ g64, const double *__restrict__ u, int64_t N, F64Params prm,
-                  StreamKPlan plan, double *__restrict__ partials, unsigned int *__restrict__ counters,
+matvec_f64_kernel(const double *__restrict__ g64, const double *__restrict__ u, int64_t N, RowBlock rb,
+                  F64Params prm, StreamKPlan plan, double *__restrict__ partials, unsigned int *__restrict__ counters,
                   double *__restrict__ y, const int *__restrict__ skip, unsigned long long *__restrict__ evaluated) {
     constexpr int BS = kF64Threads, TT = kF64TargetTile, TS = kF64SourceTile;
     if (skip != nullptr && *((volatile const int *)skip)) return;
@@ -647,7 +653,8 @@ matvec_f64_kernel(const double *__restrict__ g64, const double *__restrict__ u, 
         const int64_t s_first = p % S;
         const int64_t s_end = (S < s_first + (pend - p)) ? S : s_first + (pend - p);
         int64_t i = a * TT + tid;
-        if (i > N - 1) i = N - 1;
+        if (i > rb.nrows - 1) i = rb.nrows - 1;
+        i += rb.row0;
         const double xi = X[i], yi = Y[i], zi = Z[i], nxi = NX[i], nyi = NY[i], nzi = NZ[i];
         double acc1[1] = {0.0}, acc2[1] = {0.0};
 
@@ -690,7 +697,7 @@ matvec_f64_kernel(const double *__restrict__ g64, const double *__restrict__ u, 
             }
             acc1[0] = a1; acc2[0] = a2;
         }
-        finish_segment<TT, 1, BS>(plan, a, c, acc1, acc2, u, N, prm.diag1, prm.diag2, partials, counters, y);
+        finish_segment<TT, 1, BS>(plan, a, c, acc1, acc2, u, N, rb, prm.diag1, prm.diag2, partials, counters, y);
         p += s_end - s_first;
     }
 }
@@ -831,10 +838,80 @@ matvec_sym64_kernel(const double *__restrict__ g64, const double *__restrict__ u
 
 }  // namespace
 
+pb_status matvec_rows_launch(pb_ctx *ctx, const double *u, double *y, RowBlock rb, pb_precision prec,
+                             const int *skip_flag) {
+    if (prec != PB_FP32PAIR && prec != PB_FP64)
+        return set_error(ctx, PB_ERR_ARG, "row-block product: precision %d (FP32 pairs or FP64 only)", (int)prec);
+    if (rb.row0 < 0 || rb.nrows < 0 || rb.row0 + rb.nrows > ctx->N || rb.ld < rb.nrows)
+        return set_error(ctx, PB_ERR_ARG, "row-block product: rows [%lld, %lld) outside [0, %lld)",
+                         (long long)rb.row0, (long long)(rb.row0 + rb.nrows), (long long)ctx->N);
+    if (rb.nrows == 0) return PB_OK;
+    const double diag1 = 0.5 * (1.0 + ctx->eps), diag2 = 0.5 * (1.0 + 1.0 / ctx->eps);
+    // packed kernel with 4 targets per thread (2 for small blocks), or the plain FP64 kernel
+    const int T = rb.nrows >= 4096 ? 4 : 2;
+    const int tt = prec == PB_FP32PAIR ? kF32Threads * T : kF64TargetTile;
+    const int ts = prec == PB_FP32PAIR ? kF32SourceTile : kF64SourceTile;
+    const int occ = prec == PB_FP32PAIR ? matvec_f32_occupancy(T == 4 ? MV_F32_PACKED_T4 : MV_F32_PACKED_T2)
+                                        : matvec_occupancy(PB_FP64);
+    const StreamKPlan pl = make_plan_rows(rb.nrows, ctx->N, tt, ts, (int64_t)ctx->num_sms * occ);
+    const int64_t need_p = plan_partials(pl, tt);
+    if (need_p > ctx->rows_partials_len) {
+        if (ctx->rows_partials) ctx_free(ctx, ctx->rows_partials);
+        ctx->device_bytes -= ctx->rows_partials_len * (int64_t)sizeof(double);
+        ctx->rows_partials = nullptr;
+        ctx->rows_partials_len = 0;
+        pb_status s = ctx_alloc(ctx, (void **)&ctx->rows_partials, (size_t)need_p * sizeof(double),
+                                "row-block partials");
+        if (s != PB_OK) return s;
+        ctx->rows_partials_len = need_p;
+    }
+    if (pl.target_tiles > ctx->rows_counters_len) {
+        if (ctx->rows_counters) ctx_free(ctx, ctx->rows_counters);
+        ctx->device_bytes -= ctx->rows_counters_len * (int64_t)sizeof(unsigned int);
+        ctx->rows_counters = nullptr;
+        ctx->rows_counters_len = 0;
+        pb_status s = ctx_alloc(ctx, (void **)&ctx->rows_counters, (size_t)pl.target_tiles * sizeof(unsigned int),
+                                "row-block counters");
+        if (s != PB_OK) return s;
+        // the kernels leave every counter at zero after use
+        cudaError_t e = cudaMemsetAsync(ctx->rows_counters, 0, pl.target_tiles * sizeof(unsigned int), ctx->stream);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "row-block counters");
+        ctx->rows_counters_len = pl.target_tiles;
+    }
+    if (prec == PB_FP32PAIR) {
+        F32Params prm;
+        prm.eps = (float)ctx->eps;
+        prm.inv_eps = (float)(1.0 / ctx->eps);
+        prm.kappa = (float)ctx->kappa;
+        prm.neg_kappa_log2e = (float)(-ctx->kappa * 1.4426950408889634);
+        prm.diag1 = diag1;
+        prm.diag2 = diag2;
+        const bool k0 = ctx->kappa == 0.0;
+#define PB_LAUNCH_ROWS(T_, K0_)                                                                                   \
+    matvec_f32x2_kernel<T_, K0_><<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(                          \
+        ctx->pos32, ctx->nrm32, u, ctx->N, rb, prm, pl, ctx->rows_partials, ctx->rows_counters, y, skip_flag,    \
+        ctx->mv_count)
+        if (T == 4) {
+            if (k0) PB_LAUNCH_ROWS(4, true); else PB_LAUNCH_ROWS(4, false);
+        } else {
+            if (k0) PB_LAUNCH_ROWS(2, true); else PB_LAUNCH_ROWS(2, false);
+        }
+#undef PB_LAUNCH_ROWS
+    } else {
+        F64Params prm{ctx->eps, 1.0 / ctx->eps, ctx->kappa, diag1, diag2};
+        matvec_f64_kernel<<<(unsigned)pl.ctas, kF64Threads, 0, ctx->stream>>>(
+            ctx->g64, u, ctx->N, rb, prm, pl, ctx->rows_partials, ctx->rows_counters, y, skip_flag, ctx->mv_count);
+    }
+    PB_LAUNCHED();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PB_OK : cuda_error(ctx, e, "row-block product launch");
+}
+
 pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision prec, const int *skip_flag) {
     const double diag1 = 0.5 * (1.0 + ctx->eps), diag2 = 0.5 * (1.0 + 1.0 / ctx->eps);
     if (prec != PB_FP32PAIR && prec != PB_FP64 && prec != PB_FLOAT2)
         return set_error(ctx, PB_ERR_ARG, "pb_matvec: unknown precision %d", (int)prec);
+    if (ctx->shard.on) return shard_product(ctx, u, y, prec, skip_flag);
     {
         // the symmetric variants' scratch, allocated by the first product that needs it
         pb_status s = matvec_prepare(ctx);
@@ -862,11 +939,13 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
     do {                                                                                                        \
         if (k0)                                                                                                 \
             matvec_f32x2_kernel<T, true><<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(                   \
-                ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,    \
+                ctx->pos32, ctx->nrm32, u, ctx->N, RowBlock{0, ctx->N, ctx->N}, prm, pl, ctx->partials,                 \
+                ctx->tile_counters, y, skip_flag,                                                               \
                 ctx->mv_count);                                                                                 \
         else                                                                                                    \
             matvec_f32x2_kernel<T, false><<<(unsigned)pl.ctas, kF32Threads, 0, ctx->stream>>>(                  \
-                ctx->pos32, ctx->nrm32, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,    \
+                ctx->pos32, ctx->nrm32, u, ctx->N, RowBlock{0, ctx->N, ctx->N}, prm, pl, ctx->partials,                 \
+                ctx->tile_counters, y, skip_flag,                                                               \
                 ctx->mv_count);                                                                                 \
     } while (0)
 #define PB_LAUNCH_SYM(T, MINB)                                                                                      \
@@ -908,7 +987,8 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         F64Params prm{ctx->eps, 1.0 / ctx->eps, ctx->kappa, diag1, diag2};
         const StreamKPlan &pl = ctx->plan64;
         matvec_f64_kernel<<<(unsigned)pl.ctas, kF64Threads, 0, ctx->stream>>>(
-            ctx->g64, u, ctx->N, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag, ctx->mv_count);
+            ctx->g64, u, ctx->N, RowBlock{0, ctx->N, ctx->N}, prm, pl, ctx->partials, ctx->tile_counters, y, skip_flag,
+            ctx->mv_count);
     } else {
         F64Params prm{ctx->eps, 1.0 / ctx->eps, ctx->kappa, diag1, diag2};
         const SymPlan &sp = ctx->plansym64;

@@ -221,7 +221,8 @@ matvec_ff_kernel(const double *__restrict__ g64, const double *__restrict__ u, i
                 acc2[t] += (double)f2[t].h + (double)f2[t].l;
             }
         }
-        finish_segment<TT, T, BS>(plan, a, c, acc1, acc2, u, N, prm.diag1, prm.diag2, partials, counters, y);
+        finish_segment<TT, T, BS>(plan, a, c, acc1, acc2, u, N, RowBlock{0, N, N}, prm.diag1, prm.diag2, partials,
+                                  counters, y);
         p += s_end - s_first;
     }
 }

@@ -154,7 +154,8 @@ pb_status stage(pb_ctx *ctx, const double *src, int64_t n, double **dst, const c
 void free_all(pb_ctx *ctx) {
     void *bufs[] = {ctx->g64, ctx->pos32, ctx->nrm32, ctx->charges, ctx->b, ctx->x, ctx->partials,
                     ctx->tile_counters, ctx->red, ctx->red_counter, ctx->scalar, ctx->V, ctx->w, ctx->r,
-                    ctx->d, ctx->rres, ctx->st, ctx->sym_scratch, ctx->sym64_scratch, ctx->symff_scratch};
+                    ctx->d, ctx->rres, ctx->st, ctx->sym_scratch, ctx->sym64_scratch, ctx->symff_scratch,
+                    ctx->rows_partials, ctx->rows_counters, ctx->shard.send, ctx->shard.recv};
     for (void *p : bufs) ctx_free(ctx, p);
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);

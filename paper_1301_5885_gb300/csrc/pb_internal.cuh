@@ -76,6 +76,16 @@ __host__ __device__ inline int64_t sk_cta_of(int64_t p, int64_t W, int64_t G) {
 }
 
 StreamKPlan make_plan(int64_t n, int target_tile, int source_tile, int64_t ctas_wanted);
+// the same split for n_targets target rows against n_sources sources
+StreamKPlan make_plan_rows(int64_t n_targets, int64_t n_sources, int target_tile, int source_tile,
+                           int64_t ctas_wanted);
+
+// Target rows of a plain product: rows [row0, row0 + nrows) of both row
+// blocks of A u, the phi rows written to y[0, nrows) and the psi rows to
+// y[ld, ld + nrows); {0, N, N} is the whole product.
+struct RowBlock {
+    int64_t row0, nrows, ld;
+};
 
 // Split of the upper triangle of square tile pairs (I <= J, numbered row by
 // row) of the symmetric product over persistent CTAs, with the same range
@@ -194,6 +204,28 @@ struct pb_ctx {
     int64_t prof_launches = 0;
     unsigned long long prof_count_base = 0;
 
+    // row-block products (pb_matvec_rows and the sharded solve): their own
+    // stream-K partials and tile counters
+    double *rows_partials = nullptr;
+    int64_t rows_partials_len = 0;   // doubles
+    unsigned int *rows_counters = nullptr;
+    int64_t rows_counters_len = 0;
+
+    // row-sharded solve (pb_solve_sharded): while on, every FP32-pair or FP64
+    // product computes this rank's rows, gathers all ranks' rows through the
+    // caller's allgather and unpacks them into the full 2N vector
+    struct Shard {
+        bool on = false;
+        int world = 1, rank = 0;
+        int64_t row0 = 0, nrows = 0, per = 0;   // this rank's rows; rows per rank (padded)
+        pb_allgather_fn fn = nullptr;
+        void *user = nullptr;
+        double *send = nullptr, *recv = nullptr;
+        int64_t cap = 0;                        // doubles in recv
+        int64_t bytes = 0;                      // device bytes of send and recv
+        int64_t gathers = 0;
+    } shard;
+
     int64_t device_bytes = 0;
     char last_error[512] = {0};
 };
@@ -233,6 +265,12 @@ pb_status matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm);
 // allocates the scratch the configured FP32 variant needs (on ctx->stream), so
 // that later products allocate nothing (for example inside a stream capture)
 pb_status matvec_prepare(pb_ctx *ctx);
+// rows [rb.row0, rb.row0 + rb.nrows) of both blocks of A u into y (2 nrows:
+// phi rows, then psi rows), FP32 pairs (packed kernel) or FP64 (plain kernel)
+pb_status matvec_rows_launch(pb_ctx *ctx, const double *u, double *y, RowBlock rb, pb_precision prec,
+                             const int *skip_flag);
+// the sharded product: own rows, the caller's allgather, unpack (shard.cu)
+pb_status shard_product(pb_ctx *ctx, const double *u, double *y, pb_precision prec, const int *skip_flag);
 // matvec_ff.cu: the float-float product (PB_FLOAT2)
 StreamKPlan matvec_ff_plan(pb_ctx *ctx);
 int matvec_ff_target_tile();

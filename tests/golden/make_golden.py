@@ -47,8 +47,9 @@ def run(name: str, tol: float, checkpoint: str | None, maxit: int, restart: int 
     x0, it0, sec0 = None, 0, 0.0
     if checkpoint and os.path.exists(checkpoint):
         ck = np.load(checkpoint)
-        if (str(ck["name"]) == name and float(ck["tol"]) == tol and int(ck["restart"]) == restart
-                and ck["x"].shape == (2 * p.n,)):
+        keys = set(ck.files)
+        if ({"name", "tol", "restart", "x", "iters", "seconds", "resid"} <= keys and str(ck["name"]) == name
+                and float(ck["tol"]) == tol and int(ck["restart"]) == restart and ck["x"].shape == (2 * p.n,)):
             x0, it0, sec0 = ck["x"], int(ck["iters"]), float(ck["seconds"])
             print(f"{name}: resuming at iteration {it0}, rel. residual {float(ck['resid']):.3e}", flush=True)
     t = time.time()
