@@ -15,6 +15,9 @@ What it computes, with the passage each function follows:
   solve / solve_dense    GMRES or dense LU on Au = b, then Eq. (14)
   kirkwood_*             the analytic spherical-cavity solution (Section 3.2)
   error_linf / order     Eqs. (15)-(16)
+  yl_*                   the straightforward system of Eqs. (6)-(7) (Yoon and
+                         Lenhoff), which the paper sets aside as ill-conditioned:
+                         a CPU-only conditioning contrast, not on the GPU path
 
 Readings where the paper is silent or inconsistent:
   * eps = eps2/eps1 (the text after Eq. (11) prints eps1/eps2; only eps2/eps1
@@ -56,6 +59,9 @@ def _lib():
         lib.oracle_energy.argtypes = [_I64, _D, _D, _D, _I64, _D, ctypes.c_double, ctypes.c_double, _D, _D]
         lib.oracle_energy.restype = ctypes.c_double
         lib.oracle_gauss.argtypes = [_I64, _D, _D, _D, _I64, _D, _D]
+        lib.oracle_yl_matvec.argtypes = [_I64, _D, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D]
+        lib.oracle_yl_energy.argtypes = [_I64, _D, _D, _D, _I64, _D, _D]
+        lib.oracle_yl_energy.restype = ctypes.c_double
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
         _LIB = lib
@@ -270,6 +276,44 @@ def solve_dense(surface, charges, eps1: float, eps2: float, kappa: float) -> dic
     A = assemble(surface, eps, kappa)
     u = np.linalg.solve(A, b)
     return {"u": u, "b": b, "A": A, "energy": reaction_energy(surface, charges, eps, kappa, u)}
+
+
+# --- the straightforward (Yoon-Lenhoff) system, a conditioning contrast ----------
+def yl_matvec(surface, eps: float, kappa: float, u) -> np.ndarray:
+    """The collocated Eqs. (6)-(7) on the surface (see oracle_yl_matvec)."""
+    c, n, a = _geom(surface)
+    u = _f64(u)
+    N = a.shape[0]
+    if u.shape != (2 * N,):
+        raise ValueError("u must have length 2N")
+    y = np.empty(2 * N)
+    _lib().oracle_yl_matvec(N, _p(c), _p(n), _p(a), float(eps), float(kappa), _p(u), _p(y))
+    return y
+
+
+def yl_assemble(surface, eps: float, kappa: float) -> np.ndarray:
+    """The straightforward system's dense matrix, column by column (small N)."""
+    N = _geom(surface)[2].shape[0]
+    A = np.empty((2 * N, 2 * N))
+    e = np.zeros(2 * N)
+    for j in range(2 * N):
+        e[j] = 1.0
+        A[:, j] = yl_matvec(surface, eps, kappa, e)
+        e[j] = 0.0
+    return A
+
+
+def yl_solve(surface, charges, eps1: float, eps2: float, kappa: float, restart: int = 10, tol: float = 1e-10,
+             maxit: int = 5000) -> dict:
+    """b = [S1; 0], GMRES on the straightforward system, and its reaction energy (kcal/mol)."""
+    eps = eps2 / eps1
+    c, n, a = _geom(surface)
+    ch = _f64(charges).reshape(-1, 4)
+    N = a.shape[0]
+    b = np.concatenate([source(surface, charges, eps1)[:N], np.zeros(N)])
+    u, iters, hist, conv = gmres(lambda v: yl_matvec(surface, eps, kappa, v), b, restart, tol, maxit)
+    e = _lib().oracle_yl_energy(N, _p(c), _p(n), _p(a), ch.shape[0], _p(ch), _p(_f64(u)))
+    return {"u": u, "b": b, "energy": ENERGY_FACTOR * e, "iters": iters, "history": hist, "converged": conv}
 
 
 # --- analytic spherical cavity (Kirkwood) ---------------------------------------

@@ -206,6 +206,67 @@ void oracle_gauss(int64_t N, const double *c, const double *nrm, const double *a
     }
 }
 
+/* The straightforward system of Eqs. (6)-(7) (the coupled integral equations
+ * the paper takes from Yoon and Lenhoff and sets aside as ill-conditioned,
+ * Section 2.1), taken to x on the surface and collocated at the centroids,
+ * with the same unknowns u = [phi; dphi/dnu] (interior side) and the
+ * interface conditions phi2 = phi1, dphi2/dnu = dphi1/dnu / eps:
+ *   row i:     1/2 phi_i - sum_j S0_ij dphi_j + sum_{j != i} W_j dG0/dny(x_i, x_j) phi_j    = S1(x_i)
+ *   row N + i: 1/2 phi_i + (1/eps) sum_j Sk_ij dphi_j - sum_{j != i} W_j dGk/dny(x_i, x_j) phi_j = 0
+ * The 1/2 comes from the limit of the double-layer potential on a smooth
+ * surface (its principal value plus or minus half the density).  The
+ * single-layer matrices S0, Sk are W_j G(x_i, x_j) off the diagonal; their
+ * diagonal is the integral of G over the flat element from its centroid,
+ * taken over the disk of equal area (radius R = sqrt(W_i / pi)):
+ * R / 2 for G0 and (1 - exp(-kappa R)) / (2 kappa) for Gk.  The double-layer
+ * self term is zero on a flat element.  Output y (2N) = A_YL u. */
+void oracle_yl_matvec(int64_t N, const double *c, const double *nrm, const double *area,
+                      double eps, double kappa, const double *u, double *y)
+{
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (i = 0; i < N; ++i) {
+        double s_int = 0.0, s_ext = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) {
+                double R = sqrt(area[i] / PI_ORACLE);
+                double self0 = 0.5 * R;
+                double selfk = kappa > 0.0 ? (1.0 - exp(-kappa * R)) / (2.0 * kappa) : 0.5 * R;
+                s_int += -self0 * u[N + i];
+                s_ext += selfk / eps * u[N + i];
+                continue;
+            }
+            double d0 = c[3 * i] - c[3 * j], d1 = c[3 * i + 1] - c[3 * j + 1], d2 = c[3 * i + 2] - c[3 * j + 2];
+            if (d0 * d0 + d1 * d1 + d2 * d2 == 0.0) continue;
+            double g[8];
+            oracle_green(c + 3 * i, nrm + 3 * i, c + 3 * j, nrm + 3 * j, kappa, g);
+            s_int += area[j] * (-g[0] * u[N + j] + g[2] * u[j]);
+            s_ext += area[j] * (g[1] / eps * u[N + j] - g[3] * u[j]);
+        }
+        y[i] = 0.5 * u[i] + s_int;
+        y[N + i] = 0.5 * u[i] + s_ext;
+    }
+}
+
+/* Reaction energy of the straightforward system's solution, Eq. (6) minus
+ * the Coulomb part at each charge: 1/2 sum_k Q_k sum_j W_j [G0 dphi_j -
+ * dG0/dny phi_j], in the units of oracle_energy (G0 with its 1/(4 pi)). */
+double oracle_yl_energy(int64_t N, const double *c, const double *nrm, const double *area,
+                        int64_t Nc, const double *charges, const double *u)
+{
+    double total = 0.0;
+    for (int64_t k = 0; k < Nc; ++k) {
+        double s = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            double g[8];
+            oracle_green(charges + 4 * k, nrm + 3 * j, c + 3 * j, nrm + 3 * j, 0.0, g);
+            s += area[j] * (g[0] * u[N + j] - g[2] * u[j]);
+        }
+        total += charges[4 * k + 3] * s;
+    }
+    return 0.5 * total;
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP
