@@ -187,8 +187,37 @@ def protein_like(n_atoms: int = 2000, seed: int = 3, target_triangles: int | Non
     return Problem(f"protein_like_a{n_atoms}_s{seed}", surf, ch)
 
 
+def batch_specs(n: int = 64, seed: int = 4):
+    """The batched-solve workload's solutes: atom counts floor(exp U[ln 50,
+    ln 1500]) with about 40 triangles per atom (N ~ 2k-60k).  Returns
+    [(n_atoms, chain seed, target triangles)]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    atoms = np.floor(np.exp(rng.uniform(np.log(50), np.log(1500), size=n))).astype(int)
+    return [(int(a), 1000 + i, int(40 * a)) for i, a in enumerate(atoms)]
+
+
+def serve_specs(n: int = 64, seed: int = 5):
+    """The serving workload's solute pool: N log-uniform in [5k, 300k], atom
+    count N/150 (the 2,000-atom solute gives ~300k).  Returns
+    [(n_atoms, chain seed, target triangles)]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = np.exp(rng.uniform(np.log(5e3), np.log(3e5), size=n))
+    return [(max(20, int(x / 150)), 2000 + i, int(x)) for i, x in enumerate(ns)]
+
+
+def solute_from_spec(spec, kappa: float = KAPPA) -> Problem:
+    n_atoms, seed, target = spec
+    p = protein_like(n_atoms=n_atoms, seed=seed, target_triangles=target)
+    return Problem(p.name, p.surface, p.charges, kappa=kappa)
+
+
 def by_name(name: str) -> Problem:
-    """The named synthetic workloads used by the tests and the benchmark."""
+    """The named synthetic workloads used by the tests and the benchmark.
+    ``serve<k>_kappa<0|1>``: solute k of the 64-solute serving pool with
+    kappa 0 or 0.1257."""
+    if name.startswith("serve") and "_kappa" in name:
+        k, kap = name[len("serve"):].split("_kappa")
+        return solute_from_spec(serve_specs(64)[int(k)], kappa=(0.0 if kap == "0" else KAPPA))
     if name == "sphere1":
         return kirkwood_sphere_single()
     if name == "sphere2":
@@ -198,3 +227,58 @@ def by_name(name: str) -> Problem:
     if name == "protein300k":
         return protein_like()
     raise KeyError(name)
+
+
+def md_frames(base: Problem, n_frames: int = 20, seed: int = 7, amplitude: float = 0.2, wavelength: float = 25.0,
+              phase_step: float = 0.15, q_sigma: float = 0.02) -> list:
+    """A sequence of perturbed copies of a solute, standing in for the frames
+    of a molecular-dynamics trajectory that are solved one after another.
+
+    Frame f moves every point by a smooth displacement
+    g_f(x) = sum_m c_m [sin(w_m . x + phi_m + f omega_m) - sin(w_m . x + phi_m)]
+    (three modes, |c_m| = ``amplitude``, |w_m| = 2 pi / ``wavelength``, phases
+    advancing by about ``phase_step`` per frame), zero at frame 0.  Element centroids and charge positions move
+    with it; normals and areas follow the deformation gradient J = I + grad g
+    (Nanson's relation: n' dA' = det(J) J^-T n dA).  The partial charges get
+    seeded N(0, q_sigma) jitter per frame, shifted to keep the net charge.
+    Frame 0 is the undeformed solute with its own charges."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = 2.0 * np.pi / wavelength
+    dirs = rng.normal(size=(3, 3))
+    w = k * dirs / np.linalg.norm(dirs, axis=1, keepdims=True)
+    cvec = rng.normal(size=(3, 3))
+    cvec = amplitude * cvec / np.linalg.norm(cvec, axis=1, keepdims=True)
+    phi0 = rng.uniform(0.0, 2.0 * np.pi, size=3)
+    omega = phase_step * rng.uniform(0.5, 1.5, size=3)
+    s = base.surface
+    q0 = base.charges
+    frames = []
+    for f in range(n_frames):
+        if f == 0:
+            frames.append(Problem(f"{base.name}_frame0", s, q0.copy(), base.eps1, base.eps2, base.kappa,
+                                  base.sphere_radius))
+            continue
+
+        def disp(x):
+            arg0 = x @ w.T + phi0                    # (n, 3 modes)
+            arg = arg0 + f * omega
+            return (np.sin(arg) - np.sin(arg0)) @ cvec, np.cos(arg) - np.cos(arg0)
+
+        d, cosv = disp(s.centroids)
+        cen = s.centroids + d
+        # J = I + sum_m c_m ((cos_m(f) - cos_m(0)) w_m)^T per point
+        J = np.eye(3)[None] + np.einsum("nm,mi,mj->nij", cosv, cvec, w)
+        Jit = np.linalg.inv(J).transpose(0, 2, 1)
+        m = np.einsum("nij,nj->ni", Jit, s.normals)
+        mn = np.linalg.norm(m, axis=1)
+        nrm = m / mn[:, None]
+        area = s.areas * np.linalg.det(J) * mn
+        dq, _ = disp(q0[:, :3])
+        q = q0.copy()
+        q[:, :3] += dq
+        jit = rng.normal(0.0, q_sigma, size=q.shape[0])
+        q[:, 3] += jit - jit.mean()
+        frames.append(Problem(f"{base.name}_frame{f}", Surface(np.ascontiguousarray(cen), np.ascontiguousarray(nrm),
+                                                                np.ascontiguousarray(area)),
+                              q, base.eps1, base.eps2, base.kappa, base.sphere_radius))
+    return frames

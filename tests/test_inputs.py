@@ -91,3 +91,19 @@ def test_helix_charges():
     assert h.shape == (9, 4)
     assert np.allclose(h[:, 3], np.arange(1, 10) / 10)
     assert np.allclose(h[-1, :3], [3 / (4 * math.pi), 0.0, 2.0])
+
+
+def test_md_frames_are_small_smooth_perturbations_keeping_charges_inside():
+    import oracle
+    base = pi.protein_like(n_atoms=8, seed=1, target_triangles=None, spacing=1.6)
+    frames = pi.md_frames(base, 4)
+    assert np.array_equal(frames[0].surface.centroids, base.surface.centroids)
+    disp = [float(np.abs(f.surface.centroids - base.surface.centroids).max()) for f in frames]
+    assert disp[0] == 0.0 and 0.0 < disp[1] < disp[2] < disp[3] < 0.5
+    for f in frames:
+        assert np.allclose(np.linalg.norm(f.surface.normals, axis=1), 1.0)
+        assert np.all(f.surface.areas > 0)
+        assert abs(f.surface.areas.sum() / base.surface.areas.sum() - 1.0) < 0.01
+        assert f.charges[:, 3].sum() == pytest.approx(base.charges[:, 3].sum(), abs=1e-12)
+        g = oracle.gauss_sums(f.surface, f.charges[:, :3])
+        assert np.all(np.abs(g + 1.0) < 0.02)          # every charge still inside
