@@ -81,6 +81,9 @@ MATVEC_TRAFFIC_BYTES = {
     # profiles/matvec_sym_kernel_sphere2_full.md: both kernels of one product,
     # ncu cold-cache replay (the finishing kernel's 58 MB come from L2 in a solve)
     ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", "sphere2"): 4009472 + 1697536 + 58419712 + 25088,
+    # profiles/matvec_sym_kernel_protein300k_traffic.md: both kernels of one
+    # product on the 300,176-triangle solute (ncu, MB rounded to 0.01)
+    ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", "protein300k"): (32.61 + 657.83 + 717.82 + 4.19) * 1e6,
 }
 
 WORKLOADS = {
@@ -121,14 +124,18 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 81,920-triangle sphere line")
-    ap.add_argument("--mode", choices=["solve", "matvec", "batch", "serve", "frames"], default="solve",
+    ap.add_argument("--mode", choices=["solve", "matvec", "batch", "serve", "frames", "sharded"], default="solve",
                     help="solve: one molecule per step (default); matvec: one FP32-pair product per step; "
                          "batch: 64 solutes x 8 charge sets per step; serve: Poisson request stream through "
-                         "the solve server")
+                         "the solve server; frames: warm-started trajectory frames; sharded: one solve "
+                         "row-sharded over the job's GPUs (strong scaling, launch with torchrun for N > 1)")
     ap.add_argument("--variant", type=int, default=0,
                     help="matvec mode: FP32-pair kernel variant (0: the library's default for N)")
     ap.add_argument("--n-solutes", type=int, default=64, help="batch mode: solutes per batch")
     ap.add_argument("--frames", type=int, default=20, help="frames mode: trajectory length")
+    ap.add_argument("--batch-shape", default=None,
+                    help="batch mode: force the product shape T,row_sums,ctas_per_sm for 8 charge sets instead of "
+                         "autotuning (for profiling one shape)")
     ap.add_argument("--requests", type=int, default=200, help="serve mode: requests in the stream")
     ap.add_argument("--pool", type=int, default=64, help="serve mode: distinct solutes the requests draw from")
     ap.add_argument("--gen-workers", type=int, default=0, help="processes generating solute meshes (0: auto)")
@@ -652,6 +659,9 @@ def run_batch(args):
         ctxs = [pb.pb_create(c, n, w, q, 1.0, 80.0, 0.1257, stream=stream) for c, n, w, q in dev_in]
         ns = [c.n for c in ctxs]
         warm_info = None
+        if args.batch_shape:
+            t_, r_, c_ = (int(v) for v in args.batch_shape.split(","))
+            pb.pb_batch_force_shape(8, t_, r_, c_)
         for _ in range(args.warmup):
             _, wi = pb.pb_batch_solve(ctxs, variants, restart=args.restart, tol=args.tol, use_graph=True,
                                       raise_on_noconv=False)
@@ -933,6 +943,84 @@ def run_frames(args):
     return 0
 
 
+def run_sharded(args):
+    """One solve row-sharded over the N GPUs of the job (strong scaling): every
+    rank holds the whole surface and evaluates its rows of each product,
+    one NCCL allgather per product, GMRES replicated (pb_solve_sharded)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_1301_5885_gb300 as pb
+    import pb_inputs
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    else:
+        import socket
+        with socket.socket() as so:
+            so.bind(("127.0.0.1", 0))
+            port = so.getsockname()[1]
+        dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    prob = pb_inputs.by_name(args.workload)
+    s = prob.surface
+    n = prob.n
+    dev_in = [torch.tensor(a, device=dev) for a in (s.centroids, s.normals, s.areas, prob.charges)]
+    stream = torch.cuda.current_stream()
+    ctx = pb.pb_create(*dev_in, prob.eps1, prob.eps2, prob.kappa, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    try:
+        for _ in range(args.warmup):
+            pb.pb_solve_sharded(ctx, restart=args.restart, tol=args.tol, maxit=3000, prec="fp32pair")
+        torch.cuda.synchronize()
+        sampler = _clock_and_uuid(torch, dev)
+        dist.barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        l0 = pb.pb_kernel_launches()
+        times, infos = [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(pb.pb_solve_sharded(ctx, restart=args.restart, tol=args.tol, maxit=3000, prec="fp32pair"))
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        dist.barrier()
+        launches = pb.pb_kernel_launches() - l0
+        clocks = sampler.stop()
+    finally:
+        pb.pb_destroy(ctx)
+    total = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
+    dist.all_reduce(total, op=dist.ReduceOp.MAX)
+    total_ms = total.item()
+    if rank == 0:
+        ref = golden_energy(args.workload, prob)
+        e = infos[-1].energy_kcal
+        mv = sum(i.matvecs for i in infos)
+        line = {"metric": METRIC, "value": mv * n * (n - 1) / (total_ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f32 pairs, f64 accumulation", "data": "synthetic",
+                "config": dict(config_dict(args, prob), parallelism=f"row-sharded over {world} GPU(s)"),
+                "solves_per_s": args.steps / (total_ms * 1e-3),
+                "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
+                "energy_kcal": e, "oracle_energy_kcal": ref,
+                "rel_energy_err": abs(e - ref) / abs(ref) if ref else None,
+                "gmres": {"iters": infos[-1].iters, "matvecs": infos[-1].matvecs},
+                "note": "value counts the N(N-1) pairs of every product of the solve once, over the slowest "
+                        "rank's time; each rank evaluates its N/world rows of every product",
+                "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.tol is None:
@@ -947,6 +1035,8 @@ def main():
         return run_serve(args)
     if args.mode == "frames":
         return run_frames(args)
+    if args.mode == "sharded":
+        return run_sharded(args)
     return run_ours(args)
 
 
