@@ -723,6 +723,10 @@ def run_batch(args):
             "rel_energy_err": {"max_vs_fp64_gpu_smallest4x8": max(errs)},
             "gmres": {"iters_max": infos[-1]["iters_max"], "cycles": infos[-1]["cycles"],
                       "converged": f"{infos[-1]['converged']}/{infos[-1]['instances']}"},
+            "phases_ms": {"setup": infos[-1]["setup_ms"], "cycles": infos[-1]["cycles_ms"],
+                          "energies": infos[-1]["energy_ms"],
+                          "note": "host time of the last timed batch: set-up (vectors, FP64 source terms), "
+                                  "restart cycles, FP64 energies"},
             "roofline": {"kernel": f"bmatvec_kernel<{width}>", "bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": UNIT, "frac": achieved / peak, "traffic": None,
                          "peak_basis": f"FP32 pipe: {SMS} SMs x 128 lanes x {SM_MAX_MHZ:.0f} MHz / "

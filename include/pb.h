@@ -221,6 +221,9 @@ typedef struct {
     int tuned;              /* 1 if the autotuner ran during this call */
     int tune_candidates;    /* (shape, CTA count) pairs it timed */
     double tune_ms;         /* host time it took */
+    double setup_ms;        /* host time of the set-up: vectors, source terms, norms */
+    double cycles_ms;       /* host time of the restart cycles (tuning included) */
+    double energy_ms;       /* host time of the energies (Eq. (14), FP64) */
 } pb_batch_info;
 
 pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double *const *charges, const int64_t *nc,

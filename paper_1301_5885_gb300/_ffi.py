@@ -45,7 +45,8 @@ class _BatchInfo(ctypes.Structure):
                 ("pair_products", ctypes.c_int64), ("matvec_launches", ctypes.c_int64),
                 ("matvec_ms", ctypes.c_double), ("targets_per_thread", ctypes.c_int), ("row_sums", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("tuned", ctypes.c_int), ("tune_candidates", ctypes.c_int),
-                ("tune_ms", ctypes.c_double)]
+                ("tune_ms", ctypes.c_double), ("setup_ms", ctypes.c_double), ("cycles_ms", ctypes.c_double),
+                ("energy_ms", ctypes.c_double)]
 
 
 class _ServerOpts(ctypes.Structure):

@@ -961,12 +961,14 @@ extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double
         if (nc[s] < 0 || (nc[s] > 0 && !charges[s]))
             return set_error(lead, PB_ERR_ARG, "pb_batch_solve: bad charges for surface %d", s);
     }
+    const double t_begin = wall_seconds();
     Engine eng(lead->stream, lead->device, lead->num_sms, o.restart, o.tol, o.maxit);
     eng.autotune = true;
     std::vector<EngineMember *> mem(nsurf, nullptr);
     pb_status s = PB_OK;
     for (int i = 0; i < nsurf && s == PB_OK; ++i) mem[i] = eng.add(ctxs[i], charges[i], nc[i], nrhs[i], (uint64_t)i, &s);
     if (s != PB_OK) return set_error(lead, s, "%s", eng.error);
+    const double t_setup = wall_seconds();
     bool all = false;
     int tuned_any = 0, tune_candidates = 0;
     double tune_ms = 0.0;
@@ -982,6 +984,7 @@ extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double
         for (EngineMember *mb : mem) all &= mb->finished;
     }
     if (s != PB_OK) return set_error(lead, s, "%s", eng.error);
+    const double t_cycles = wall_seconds();
     int k = 0, nconv = 0, nq = 0, iters_max = 0;
     int64_t iters_sum = 0;
     double resid_max = 0.0;
@@ -1001,7 +1004,11 @@ extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double
         k += nrhs[i];
     }
     if (s != PB_OK) return set_error(lead, s, "%s", eng.error);
+    const double t_end = wall_seconds();
     if (info) {
+        info->setup_ms = 1e3 * (t_setup - t_begin);
+        info->cycles_ms = 1e3 * (t_cycles - t_setup);
+        info->energy_ms = 1e3 * (t_end - t_cycles);
         info->instances = nq;
         info->converged = nconv;
         info->cycles = eng.cycles_run;
