@@ -84,11 +84,15 @@ energy_kernel(const double *__restrict__ g64, const float4 *__restrict__ pos32, 
     __shared__ Charge4 s_q[kChargeTile];
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kSrcThreads;
-    for (int64_t k0 = 0; k0 < nc; k0 += kChargeTile) {
+    // blockIdx.y takes the charges [kbeg, kend): a second grid dimension
+    // keeps small surfaces from leaving most SMs idle
+    const int64_t kchunk = (nc + gridDim.y - 1) / gridDim.y;
+    const int64_t kbeg = blockIdx.y * kchunk, kend = (kbeg + kchunk < nc) ? kbeg + kchunk : nc;
+    for (int64_t k0 = kbeg; k0 < kend; k0 += kChargeTile) {
         __syncthreads();
-        if (k0 + threadIdx.x < nc) s_q[threadIdx.x] = ch[k0 + threadIdx.x];
+        if (k0 + threadIdx.x < kend) s_q[threadIdx.x] = ch[k0 + threadIdx.x];
         __syncthreads();
-        const int cnt = (int)((nc - k0) < kChargeTile ? (nc - k0) : kChargeTile);
+        const int cnt = (int)((kend - k0) < kChargeTile ? (kend - k0) : kChargeTile);
         for (int64_t j = blockIdx.x * (int64_t)kSrcThreads + threadIdx.x; j < N; j += stride) {
             const double phi = u[j], dphi = u[N + j];
             if (F32) {
@@ -134,11 +138,12 @@ energy_kernel(const double *__restrict__ g64, const float4 *__restrict__ pos32, 
         }
     }
     const double bs = block_sum<kSrcThreads>(acc);
-    if (threadIdx.x == 0) red[blockIdx.x] = bs;
-    if (last_block_arrived(counter, gridDim.x)) {
+    const unsigned int nblocks = gridDim.x * gridDim.y;
+    if (threadIdx.x == 0) red[blockIdx.y * gridDim.x + blockIdx.x] = bs;
+    if (last_block_arrived(counter, nblocks)) {
         if (threadIdx.x == 0) {
             double t = 0.0;
-            for (unsigned int b2 = 0; b2 < gridDim.x; ++b2) t += __ldcg(red + b2);
+            for (unsigned int b2 = 0; b2 < nblocks; ++b2) t += __ldcg(red + b2);
             out[0] = 0.5 * kCoulombKcal * t;
             *counter = 0u;
         }
@@ -163,7 +168,18 @@ pb_status source_launch(pb_ctx *ctx, double *b, pb_precision prec) {
 }
 
 pb_status energy_launch(pb_ctx *ctx, const double *u, pb_precision prec, double *dev_out) {
-    const int blocks = red_blocks(ctx, ctx->N);
+    // about 8 blocks per SM (FP64 pair arithmetic needs many warps to hide
+    // its latency): source blocks first, then the charges split over a
+    // second grid dimension (chunks of at least 32 charges); the grid depends
+    // only on N, Nc and the SM count, so the summation order is fixed
+    const int64_t want = 8 * (int64_t)ctx->num_sms;
+    int64_t bx = red_blocks(ctx, ctx->N);
+    int64_t by = want / bx;
+    const int64_t ymax = (ctx->Nc + 31) / 32;
+    if (by > ymax) by = ymax;
+    if (by < 1) by = 1;
+    if (bx * by > ctx->red_len) by = ctx->red_len / bx > 0 ? ctx->red_len / bx : 1;
+    const dim3 blocks((unsigned)bx, (unsigned)by);
     if (prec == PB_FP32PAIR)
         energy_kernel<true><<<blocks, kSrcThreads, 0, ctx->stream>>>(ctx->g64, ctx->pos32, ctx->nrm32, ctx->N,
                                                                      ctx->charges, ctx->Nc, u, ctx->eps, ctx->kappa,
