@@ -725,8 +725,8 @@ def run_batch(args):
                       "converged": f"{infos[-1]['converged']}/{infos[-1]['instances']}"},
             "phases_ms": {"setup": infos[-1]["setup_ms"], "cycles": infos[-1]["cycles_ms"],
                           "energies": infos[-1]["energy_ms"],
-                          "note": "host time of the last timed batch: set-up (vectors, FP64 source terms), "
-                                  "restart cycles, FP64 energies"},
+                          "note": "host time of the last timed batch: set-up (vectors, float-float source terms), "
+                                  "restart cycles, float-float energies"},
             "roofline": {"kernel": f"bmatvec_kernel<{width}>", "bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": UNIT, "frac": achieved / peak, "traffic": None,
                          "peak_basis": f"FP32 pipe: {SMS} SMs x 128 lanes x {SM_MAX_MHZ:.0f} MHz / "

@@ -65,9 +65,9 @@ typedef enum {
                              N = 2,048 each unordered pair is evaluated once
                              for both rows, with device scratch of about
                              8 N^2 / 256 bytes allocated by the first such
-                             product.  Accepted by pb_matvec and pb_solve
-                             (prec, refine_prec); pb_source and pb_energy_of
-                             reject it. */
+                             product.  Accepted by pb_matvec, pb_solve
+                             (prec, refine_prec), pb_source and pb_energy_of
+                             (the N x Nc pair sums of Eqs. (11) and (14)). */
 } pb_precision;
 
 typedef struct {
@@ -136,13 +136,16 @@ pb_status pb_matvec(pb_ctx *ctx, const double *u, double *y, pb_precision prec);
 
 /* Solve A u = b with restarted GMRES on the device (Section 2.4; x0 = 0 unless
  * x0 is given, restarts continue from the current approximation), then
- * evaluate Eq. (14).  x0: device 2N or NULL.  x_out: device 2N or NULL; the
+ * evaluate Eq. (14).  The source term b and the energy take FP64 pairs when
+ * prec is PB_FP64 (the plain path) and float-float pairs otherwise (about
+ * 1e-12 relative per pair term, on the FP32 pipe).  x0: device 2N or NULL.  x_out: device 2N or NULL; the
  * solution is also kept in the context for pb_energy.  info may be NULL.
  * Returns PB_ERR_NOCONV (solution and info still filled) if maxit is reached. */
 pb_status pb_solve(pb_ctx *ctx, const pb_solve_opts *opts, const double *x0, double *x_out,
                    pb_solve_info *info);
 
-/* Eq. (14) for the solution of the last successful pb_solve, FP64 pairs. */
+/* Eq. (14) for the solution of the last successful pb_solve, in the pair
+ * arithmetic that solve used for its energy. */
 pb_status pb_energy(pb_ctx *ctx, double *energy_kcal);
 
 /* Eq. (14) for an arbitrary device vector u (2N): (1/2) sum_k Q_k phi_reac(x_k). */

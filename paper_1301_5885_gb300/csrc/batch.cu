@@ -396,7 +396,7 @@ EngineMember *Engine::add(pb_ctx *surf, const double *charges_host, int64_t nc, 
         double *b = mb->vec + (size_t)r * per;
         surf->charges = mb->q + r * nc;
         surf->Nc = nc;
-        *st = source_launch(surf, b, PB_FP64);
+        *st = source_launch(surf, b, PB_FLOAT2);
         if (*st == PB_OK) *st = norm2_launch(surf, b, n2, &mb->st[r].bnorm);
     }
     surf->charges = keep_q;
@@ -916,7 +916,7 @@ pb_status Engine::energies(EngineMember *mb, double *out) {
     for (int r = 0; r < mb->nrhs && s == PB_OK; ++r) {
         c->charges = mb->q + r * mb->nc;
         c->Nc = mb->nc;
-        s = energy_launch(c, mb->vec + (size_t)r * per + n2, PB_FP64, scalar_ + (r % 64));
+        s = energy_launch(c, mb->vec + (size_t)r * per + n2, PB_FLOAT2, scalar_ + (r % 64));
     }
     c->charges = keep_q;
     c->Nc = keep_nc;

@@ -51,7 +51,8 @@ class Engine {
     ~Engine();
 
     // Adds a surface with nrhs host charge sets of nc rows (x, y, z, Q):
-    // allocates its vectors, computes b = [S1; S2] (Eq. (11)) and ||b||, and
+    // allocates its vectors, computes b = [S1; S2] (Eq. (11), float-float
+    // pairs) and ||b||, and
     // initialises its GMRES states (x0 = 0).  Returns the member, or null.
     EngineMember *add(pb_ctx *surf, const double *charges_host, int64_t nc, int nrhs, uint64_t tag, pb_status *st);
     // Frees a member's device memory and drops it from the set.
@@ -61,7 +62,7 @@ class Engine {
     // time_products (no graph), the product launches are bracketed by CUDA
     // events and their time is added to matvec_ms.
     pb_status cycle(bool use_graph, bool time_products = false);
-    // Eq. (14) for every instance of a member (FP64 pairs), kcal/mol.
+    // Eq. (14) for every instance of a member (float-float pairs), kcal/mol.
     pb_status energies(EngineMember *m, double *out);
     // Bytes one member of N triangles with nrhs sets needs (vectors and states).
     static int64_t member_bytes(int64_t N, int nrhs, int m);

@@ -24,6 +24,7 @@
 #include "fastmath.cuh"
 #include "finish.cuh"
 #include "pb_internal.cuh"
+#include "reduce.cuh"
 #include "sym.cuh"
 
 namespace pb {
@@ -386,7 +387,131 @@ StreamKPlan matvec_ff_plan(pb_ctx *ctx) {
 
 int matvec_ff_target_tile() { return kFFTargetTile; }
 
-pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *skip_flag) {
+// ---------------------------------------------------------------------------
+// The source term of Eq. (11) and the energy of Eq. (14) in float-float: the
+// same N x Nc pair sums as the FP64 kernels (source_energy.cu), with every
+// pair quantity and the per-tile sums in float-float on the FP32 pipe and the
+// final sums in FP64.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kFFChargeThreads = 256;
+constexpr int kFFChargeTile = 256;
+
+// charges as float-float {x, y}, {z, q} (hi, lo pairs)
+__device__ __forceinline__ void ff_stage_charge(const Charge4 &q, float4 *dst) {
+    const ff x = ff_make(q.x), y = ff_make(q.y), z = ff_make(q.z), w = ff_make(q.q);
+    dst[0] = make_float4(x.h, x.l, y.h, y.l);
+    dst[1] = make_float4(z.h, z.l, w.h, w.l);
+}
+
+// 1/rho from the MUFU rsqrt and one Newton step in float-float
+__device__ __forceinline__ ff ff_rsqrt(ff r2) {
+    const float y0 = rsqrt_approx(r2.h);
+    const float y0y0 = y0 * y0;
+    const ff yy{y0y0, fmaf(y0, y0, -y0y0)};
+    const ff h = ff_mul(r2, yy);
+    const ff corr = ff_add_q(ff{1.5f, 0.f}, ff{-0.5f * h.h, -0.5f * h.l});
+    return ff_mulf(corr, y0);
+}
+
+// b_i = scale sum_k Q_k / rho_ik, b_{N+i} = scale sum_k -Q_k c_x / rho_ik^3
+// (S1, S2 of Eq. (11) with scale = 1 / (4 pi eps1)); one thread per target
+__global__ void __launch_bounds__(kFFChargeThreads)
+ff_source_kernel(const double *__restrict__ g64, int64_t N, const Charge4 *__restrict__ ch, int64_t nc, double scale,
+                 double *__restrict__ b) {
+    __shared__ float4 s_q[kFFChargeTile][2];
+    const int64_t i0 = blockIdx.x * (int64_t)kFFChargeThreads + threadIdx.x;
+    const int64_t i = i0 < N ? i0 : N - 1;
+    const ff xi = ff_make(g64[i]), yi = ff_make(g64[N + i]), zi = ff_make(g64[2 * N + i]);
+    const ff nxi = ff_make(g64[3 * N + i]), nyi = ff_make(g64[4 * N + i]), nzi = ff_make(g64[5 * N + i]);
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t k0 = 0; k0 < nc; k0 += kFFChargeTile) {
+        __syncthreads();
+        if (k0 + threadIdx.x < nc) ff_stage_charge(ch[k0 + threadIdx.x], s_q[threadIdx.x]);
+        __syncthreads();
+        const int cnt = (int)((nc - k0) < kFFChargeTile ? (nc - k0) : kFFChargeTile);
+        ff a1{0.f, 0.f}, a2{0.f, 0.f};
+        for (int k = 0; k < cnt; ++k) {
+            const float4 A = s_q[k][0], B = s_q[k][1];
+            const ff dx = ff_sub(xi, ff{A.x, A.y}), dy = ff_sub(yi, ff{A.z, A.w}), dz = ff_sub(zi, ff{B.x, B.y});
+            const ff r2 = ff_add_q(ff_add_q(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
+            if (!(r2.h > 0.f)) continue;
+            const ff inv = ff_rsqrt(r2);
+            const ff q{B.z, B.w};
+            const ff cx = ff_add(ff_add(ff_mul(dx, nxi), ff_mul(dy, nyi)), ff_mul(dz, nzi));
+            const ff inv3 = ff_mul(ff_mul(inv, inv), inv);
+            a1 = ff_add(a1, ff_mul(q, inv));
+            a2 = ff_sub(a2, ff_mul(ff_mul(q, cx), inv3));
+        }
+        s1 += (double)a1.h + (double)a1.l;
+        s2 += (double)a2.h + (double)a2.l;
+    }
+    if (i0 < N) {
+        b[i0] = scale * s1;
+        b[N + i0] = scale * s2;
+    }
+}
+
+// 1/2 sum_k Q_k sum_j W_j [K1(x_k, x_j) dphi_j + K2(x_k, x_j) phi_j] in kcal/mol
+// (Eq. (14)); sources over blockIdx.x and threads, charges split over
+// blockIdx.y; fixed-order two-stage reduction finished by the last block.
+__global__ void __launch_bounds__(kFFChargeThreads)
+ff_energy_kernel(const double *__restrict__ g64, int64_t N, const Charge4 *__restrict__ ch, int64_t nc,
+                 const double *__restrict__ u, FFParams prm, double *__restrict__ red,
+                 unsigned int *__restrict__ counter, double *__restrict__ out) {
+    __shared__ float4 s_q[kFFChargeTile][2];
+    const ff one{1.f, 0.f};
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kFFChargeThreads;
+    const int64_t kchunk = (nc + gridDim.y - 1) / gridDim.y;
+    const int64_t kbeg = blockIdx.y * kchunk, kend = (kbeg + kchunk < nc) ? kbeg + kchunk : nc;
+    for (int64_t k0 = kbeg; k0 < kend; k0 += kFFChargeTile) {
+        __syncthreads();
+        if (k0 + threadIdx.x < kend) ff_stage_charge(ch[k0 + threadIdx.x], s_q[threadIdx.x]);
+        __syncthreads();
+        const int cnt = (int)((kend - k0) < kFFChargeTile ? (kend - k0) : kFFChargeTile);
+        for (int64_t j = blockIdx.x * (int64_t)kFFChargeThreads + threadIdx.x; j < N; j += stride) {
+            const ff xj = ff_make(g64[j]), yj = ff_make(g64[N + j]), zj = ff_make(g64[2 * N + j]);
+            const ff nx = ff_make(g64[3 * N + j]), ny = ff_make(g64[4 * N + j]), nz = ff_make(g64[5 * N + j]);
+            ff a1{0.f, 0.f}, a2{0.f, 0.f};   // sum_k Q_k K1, sum_k Q_k K2 (K without the 1/(4 pi))
+            for (int k = 0; k < cnt; ++k) {
+                const float4 A = s_q[k][0], B = s_q[k][1];
+                const ff dx = ff_sub(ff{A.x, A.y}, xj), dy = ff_sub(ff{A.z, A.w}, yj), dz = ff_sub(ff{B.x, B.y}, zj);
+                const ff r2 = ff_add_q(ff_add_q(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
+                if (!(r2.h > 0.f)) continue;
+                const ff inv = ff_rsqrt(r2);
+                const ff rho = ff_mul(r2, inv);
+                const ff e = ff_exp2(ff_mul(prm.neg_kappa_log2e, rho), prm);
+                const ff e1 = ff_add_q(e, ff_mul(e, ff_mul(prm.kappa, rho)));     // e (1 + kappa rho)
+                const ff cy = ff_add(ff_add(ff_mul(dx, nx), ff_mul(dy, ny)), ff_mul(dz, nz));
+                const ff q{B.z, B.w};
+                a1 = ff_add(a1, ff_mul(q, ff_mul(ff_sub(one, e), inv)));
+                a2 = ff_add(a2, ff_mul(ff_mul(q, ff_sub(ff_mul(prm.eps, e1), one)),
+                                       ff_mul(cy, ff_mul(ff_mul(inv, inv), inv))));
+            }
+            acc += g64[6 * N + j] * (((double)a1.h + (double)a1.l) * u[N + j] + ((double)a2.h + (double)a2.l) * u[j]);
+        }
+    }
+    const double bs = block_sum<kFFChargeThreads>(acc);
+    const unsigned int nblocks = gridDim.x * gridDim.y;
+    if (threadIdx.x == 0) red[blockIdx.y * gridDim.x + blockIdx.x] = bs;
+    if (last_block_arrived(counter, nblocks)) {
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (unsigned int b2 = 0; b2 < nblocks; ++b2) t += __ldcg(red + b2);
+            out[0] = 0.5 * kCoulombKcal * t;
+            *counter = 0u;
+        }
+    }
+}
+
+}  // namespace
+
+namespace {
+
+// The 2^(k/64) table (uploaded once per device) and the pair constants.
+pb_status ff_setup(pb_ctx *ctx, FFParams *out) {
     const int dev = ctx->device;
     {
         // the 2^(k/64) table, uploaded once per device (synchronously, so that
@@ -417,6 +542,16 @@ pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *
     prm.ln2 = mk(0.69314718055994530942);
     prm.diag1 = 0.5 * (1.0 + ctx->eps);
     prm.diag2 = 0.5 * (1.0 + 1.0 / ctx->eps);
+    *out = prm;
+    return PB_OK;
+}
+
+}  // namespace
+
+pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *skip_flag) {
+    FFParams prm;
+    pb_status fs = ff_setup(ctx, &prm);
+    if (fs != PB_OK) return fs;
     if (ctx->N < kFFSymMinN) {
         const StreamKPlan &pl = ctx->planff;
         matvec_ff_kernel<<<(unsigned)pl.ctas, kFFThreads, 0, ctx->stream>>>(
@@ -456,6 +591,38 @@ pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *
     }
     PB_LAUNCHED();   // the finishing kernel (the caller counts the first)
     return PB_OK;
+}
+
+pb_status source_ff_launch(pb_ctx *ctx, double *b) {
+    FFParams prm;
+    pb_status fs = ff_setup(ctx, &prm);
+    if (fs != PB_OK) return fs;
+    const unsigned blocks = (unsigned)((ctx->N + kFFChargeThreads - 1) / kFFChargeThreads);
+    ff_source_kernel<<<blocks, kFFChargeThreads, 0, ctx->stream>>>(ctx->g64, ctx->N, ctx->charges, ctx->Nc,
+                                                                  kInv4Pi / ctx->eps1, b);
+    PB_LAUNCHED();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PB_OK : cuda_error(ctx, e, "float-float source kernel");
+}
+
+pb_status energy_ff_launch(pb_ctx *ctx, const double *u, double *dev_out) {
+    FFParams prm;
+    pb_status fs = ff_setup(ctx, &prm);
+    if (fs != PB_OK) return fs;
+    // the grid of the FP64 energy kernel: about 8 blocks per SM, charges
+    // split over the second dimension; fixed for given N, Nc and SM count
+    const int64_t want = 8 * (int64_t)ctx->num_sms;
+    int64_t bx = red_blocks(ctx, ctx->N);
+    int64_t by = want / bx;
+    const int64_t ymax = (ctx->Nc + 31) / 32;
+    if (by > ymax) by = ymax;
+    if (by < 1) by = 1;
+    if (bx * by > ctx->red_len) by = ctx->red_len / bx > 0 ? ctx->red_len / bx : 1;
+    ff_energy_kernel<<<dim3((unsigned)bx, (unsigned)by), kFFChargeThreads, 0, ctx->stream>>>(
+        ctx->g64, ctx->N, ctx->charges, ctx->Nc, u, prm, ctx->red, ctx->red_counter, dev_out);
+    PB_LAUNCHED();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PB_OK : cuda_error(ctx, e, "float-float energy kernel");
 }
 
 }  // namespace pb

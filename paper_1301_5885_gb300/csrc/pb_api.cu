@@ -405,7 +405,8 @@ pb_status pb_set_charges(pb_ctx *ctx, const double *charges, int64_t Nc) {
 
 pb_status pb_source(pb_ctx *ctx, double *b, pb_precision prec) {
     if (!ctx || !b) return set_error(ctx, PB_ERR_ARG, "pb_source: NULL argument");
-    if (prec != PB_FP64 && prec != PB_FP32PAIR) return set_error(ctx, PB_ERR_ARG, "pb_source: unknown precision");
+    if (prec != PB_FP64 && prec != PB_FP32PAIR && prec != PB_FLOAT2)
+        return set_error(ctx, PB_ERR_ARG, "pb_source: unknown precision");
     return source_launch(ctx, b, prec);
 }
 
@@ -423,9 +424,13 @@ pb_status pb_solve(pb_ctx *ctx, const pb_solve_opts *opts, const double *x0, dou
     const int64_t N2 = 2 * ctx->N;
     cudaError_t e;
     ctx->x_valid = false;
-    if (!ctx->b_valid) {
-        if ((s = source_launch(ctx, ctx->b, PB_FP64)) != PB_OK) return s;
+    // the source term and the energy: FP64 pairs on the plain FP64 path,
+    // float-float pairs (FP64-level, on the FP32 pipe) otherwise
+    const pb_precision side = o.prec == PB_FP64 ? PB_FP64 : PB_FLOAT2;
+    if (!ctx->b_valid || ctx->b_prec != side) {
+        if ((s = source_launch(ctx, ctx->b, side)) != PB_OK) return s;
         ctx->b_valid = true;
+        ctx->b_prec = side;
     }
     if (x0) {
         e = cudaMemcpyAsync(ctx->x, x0, N2 * sizeof(double), cudaMemcpyDefault, ctx->stream);
@@ -474,7 +479,8 @@ pb_status pb_solve(pb_ctx *ctx, const pb_solve_opts *opts, const double *x0, dou
         rel = rel64;
     }
     double E = 0.0;
-    if ((s = energy_launch(ctx, ctx->x, PB_FP64, ctx->scalar)) != PB_OK) return s;
+    if ((s = energy_launch(ctx, ctx->x, side, ctx->scalar)) != PB_OK) return s;
+    ctx->e_prec = side;
     if ((s = read_scalar(ctx, ctx->scalar, &E)) != PB_OK) return s;
     if (x_out) {
         e = cudaMemcpyAsync(x_out, ctx->x, N2 * sizeof(double), cudaMemcpyDefault, ctx->stream);
@@ -499,14 +505,15 @@ pb_status pb_solve(pb_ctx *ctx, const pb_solve_opts *opts, const double *x0, dou
 pb_status pb_energy(pb_ctx *ctx, double *energy_kcal) {
     if (!ctx || !energy_kcal) return set_error(ctx, PB_ERR_ARG, "pb_energy: NULL argument");
     if (!ctx->x_valid) return set_error(ctx, PB_ERR_ARG, "pb_energy: no solution (call pb_solve first)");
-    pb_status s = energy_launch(ctx, ctx->x, PB_FP64, ctx->scalar);
+    pb_status s = energy_launch(ctx, ctx->x, ctx->e_prec, ctx->scalar);
     if (s != PB_OK) return s;
     return read_scalar(ctx, ctx->scalar, energy_kcal);
 }
 
 pb_status pb_energy_of(pb_ctx *ctx, const double *u, pb_precision prec, double *energy_kcal) {
     if (!ctx || !u || !energy_kcal) return set_error(ctx, PB_ERR_ARG, "pb_energy_of: NULL argument");
-    if (prec != PB_FP64 && prec != PB_FP32PAIR) return set_error(ctx, PB_ERR_ARG, "pb_energy_of: unknown precision");
+    if (prec != PB_FP64 && prec != PB_FP32PAIR && prec != PB_FLOAT2)
+        return set_error(ctx, PB_ERR_ARG, "pb_energy_of: unknown precision");
     pb_status s = energy_launch(ctx, u, prec, ctx->scalar);
     if (s != PB_OK) return s;
     return read_scalar(ctx, ctx->scalar, energy_kcal);

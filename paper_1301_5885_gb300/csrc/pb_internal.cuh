@@ -150,6 +150,8 @@ struct pb_ctx {
     double *b = nullptr;         // right-hand side for the current charges
     double *x = nullptr;         // last solution
     bool b_valid = false, x_valid = false;
+    pb_precision b_prec = PB_FP64;   // pair arithmetic of the stored b
+    pb_precision e_prec = PB_FP64;   // of the last solve's energy (pb_energy repeats it)
 
     // matvec scratch: per (target tile, segment) partial row sums, and one
     // arrival counter per target tile (left at zero between launches)
@@ -275,6 +277,9 @@ pb_status shard_product(pb_ctx *ctx, const double *u, double *y, pb_precision pr
 StreamKPlan matvec_ff_plan(pb_ctx *ctx);
 int matvec_ff_target_tile();
 pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *skip_flag);
+// Eq. (11) and Eq. (14) with float-float pair arithmetic (matvec_ff.cu)
+pb_status source_ff_launch(pb_ctx *ctx, double *b);
+pb_status energy_ff_launch(pb_ctx *ctx, const double *u, double *dev_out);
 // FP64 product variant (Matvec64Variant); the symmetric ones allocate their
 // scratch with their first product
 pb_status matvec_configure_fp64(pb_ctx *ctx, int variant);

@@ -153,6 +153,7 @@ energy_kernel(const double *__restrict__ g64, const float4 *__restrict__ pos32, 
 }  // namespace
 
 pb_status source_launch(pb_ctx *ctx, double *b, pb_precision prec) {
+    if (prec == PB_FLOAT2) return source_ff_launch(ctx, b);
     const unsigned blocks = (unsigned)((ctx->N + kSrcThreads - 1) / kSrcThreads);
     const double scale = kInv4Pi / ctx->eps1;
     if (prec == PB_FP32PAIR)
@@ -168,6 +169,7 @@ pb_status source_launch(pb_ctx *ctx, double *b, pb_precision prec) {
 }
 
 pb_status energy_launch(pb_ctx *ctx, const double *u, pb_precision prec, double *dev_out) {
+    if (prec == PB_FLOAT2) return energy_ff_launch(ctx, u, dev_out);
     // about 8 blocks per SM (FP64 pair arithmetic needs many warps to hide
     // its latency): source blocks first, then the charges split over a
     // second grid dimension (chunks of at least 32 charges); the grid depends

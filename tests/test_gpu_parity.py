@@ -263,7 +263,7 @@ def test_matvec_is_deterministic(prec):
     assert np.array_equal(y1, y2)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32pair", 2e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("float2", 1e-12), ("fp32pair", 2e-6)])
 def test_source_matches_oracle(prec, tol):
     pb = _pb()
     p = pi.kirkwood_sphere_multi(level=4, radius=10.0, n_charges=300, seed=3)
@@ -276,7 +276,7 @@ def test_source_matches_oracle(prec, tol):
     assert np.linalg.norm(b - ref) <= tol * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32pair", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("float2", 1e-10), ("fp32pair", 1e-5)])
 def test_energy_of_matches_oracle(prec, tol):
     pb = _pb()
     p = pi.kirkwood_sphere_multi(level=3, radius=8.0, n_charges=280, seed=6)
@@ -356,11 +356,26 @@ def test_float2_is_rejected_where_it_has_no_meaning():
     pb = _pb()
     surf = pi.icosphere(2.0, 1)
     with _ctx(surf, np.array([[0.0, 0.0, 0.0, 1.0]])) as ctx:
-        b = torch.empty(2 * surf.n, dtype=torch.float64, device="cuda")
-        with pytest.raises(pb.PBError):
-            pb.pb_source(ctx, b, "float2")
         with pytest.raises(pb.PBError):
             pb.pb_solve(ctx, prec="fp32pair", refine=1, refine_prec="fp32pair")
+
+
+@pytest.mark.parametrize("kappa", [0.1257, 0.0])
+def test_float2_source_and_energy_match_the_oracle_on_a_solute(kappa):
+    """The float-float N x Nc pair sums (the source term and energy of the
+    FP32-pair and float-float solves) on a protein-like surface with charges
+    close to it, at the FP64 bound."""
+    pb = _pb()
+    p = pi.protein_like(n_atoms=30, seed=9, target_triangles=None, spacing=1.2)
+    u = _u(p.n, 19) * 1e-2
+    with _ctx(p.surface, p.charges, kappa=kappa) as ctx:
+        b = torch.empty(2 * p.n, dtype=torch.float64, device="cuda")
+        pb.pb_source(ctx, b, "float2")
+        torch.cuda.synchronize()
+        e = pb.pb_energy_of(ctx, torch.tensor(u, device="cuda"), "float2")
+    ref_b = oracle.source(p.surface, p.charges, 1.0)
+    assert_blocks_close(b.cpu().numpy(), ref_b, (1e-12, 1e-11))
+    assert e == pytest.approx(oracle.reaction_energy(p.surface, p.charges, 80.0, kappa, u), rel=1e-10)
 
 
 def test_cached_memory_release_keeps_live_contexts_working():
