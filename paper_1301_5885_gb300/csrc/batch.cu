@@ -277,6 +277,38 @@ __global__ void bg_flags(const BSurf *__restrict__ surf, int nsurf, const BInst 
     act_ax[nsurf + s] = !ax;
 }
 
+// The work split of one batched product over the surfaces with a running
+// instance: wbase[s] = sum of ntiles S over the active surfaces before s,
+// wbase[nsurf] = the total (surfaces without a running instance get none, so
+// the product's CTAs share only live work).  One block; a prefix sum over
+// shared-memory chunks by one thread.
+__global__ void bmv_plan_kernel(const BSurf *__restrict__ surf, int nsurf, const int *__restrict__ act,
+                                int64_t *__restrict__ wbase) {
+    constexpr int CH = 1024;
+    __shared__ int64_t s_w[CH];
+    __shared__ int64_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    for (int c0 = 0; c0 < nsurf; c0 += CH) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < CH; i += blockDim.x) {
+            const int s = c0 + i;
+            s_w[i] = (s < nsurf && vol(act + s)) ? surf[s].ntiles * surf[s].S : 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t c = s_carry;
+            const int n = (nsurf - c0) < CH ? (nsurf - c0) : CH;
+            for (int i = 0; i < n; ++i) {
+                wbase[c0 + i] = c;
+                c += s_w[i];
+            }
+            s_carry = c;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) wbase[nsurf] = s_carry;
+}
+
 __global__ void bg_status(const BInst *__restrict__ inst, int nq, BStatus *out) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
@@ -300,7 +332,7 @@ Engine::~Engine() {
         delete mb;
     }
     void *bufs[] = {d_surf_, d_inst_, d_ch_, cnt_inst_, cnt_tile_, evals_, act_step_, act_ax_, red_, part_, scalar_,
-                    d_status_};
+                    d_status_, d_wbase_};
     for (void *p : bufs)
         if (p) cudaFreeAsync(p, stream_);
     if (gexec_) cudaGraphExecDestroy(gexec_);
@@ -452,13 +484,13 @@ BmvConfig default_config(int R) {
     return c;
 }
 
-BmvArgs bmv_args(const BSurf *surf, int nsurf, const BInst *inst, int64_t W, int64_t G, int usel, int k,
+BmvArgs bmv_args(const BSurf *surf, int nsurf, const BInst *inst, const int64_t *wbase, int64_t G, int usel, int k,
                  const int *act, double *part, unsigned int *cnt, unsigned long long *evals) {
     BmvArgs a;
     a.surf = surf;
     a.nsurf = nsurf;
     a.inst = inst;
-    a.W = W;
+    a.wbase = wbase;
     a.G = G;
     a.usel = usel;
     a.k = k;
@@ -477,6 +509,7 @@ void Engine::retile(std::vector<BSurf> &hs, const std::vector<char> &direct, int
         const int64_t nt = direct[i] ? 0 : (hs[i].N + TT - 1) / TT;
         hs[i].tile_base = t;
         hs[i].work_base = w;
+        hs[i].ntiles = nt;
         t += nt;
         w += nt * hs[i].S;
     }
@@ -514,7 +547,10 @@ pb_status Engine::tune(std::vector<BSurf> &hs, const std::vector<char> &direct, 
             if (G > W) G = W;
             // every surface with a running instance takes part (the Arnoldi-step
             // flags; the x-product flags are off for instances that start at x = 0)
-            const BmvArgs a = bmv_args(d_surf_, nsurf_, d_inst_, W, G, 0, 0, act_step_, part_, cnt_tile_, evals_);
+            const BmvArgs a = bmv_args(d_surf_, nsurf_, d_inst_, d_wbase_, G, 0, 0, act_step_, part_, cnt_tile_,
+                                       evals_);
+            bmv_plan_kernel<<<1, 256, 0, stream_>>>(d_surf_, nsurf_, act_step_, d_wbase_);
+            count_launch();
             e = bmatvec_dispatch(R_, sh[i], a, (unsigned)G, stream_, nullptr);
             if (e == cudaSuccess) e = cudaEventRecord(e0, stream_);
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) e = bmatvec_dispatch(R_, sh[i], a, (unsigned)G, stream_, nullptr);
@@ -693,6 +729,7 @@ pb_status Engine::rebuild() {
     }
     pb_status s = PB_OK;
     if (s == PB_OK) s = grow((void **)&d_surf_, &cap_surf_, nsurf_, sizeof(BSurf), "engine surfaces");
+    if (s == PB_OK) s = grow((void **)&d_wbase_, &cap_wbase_, nsurf_ + 1, sizeof(int64_t), "engine work split");
     if (s == PB_OK) s = grow((void **)&d_inst_, &cap_inst_, nq_, sizeof(BInst), "engine instances");
     if (s == PB_OK) s = grow((void **)&d_ch_, &cap_ch_, nchunks_, sizeof(BChunk), "engine chunks");
     if (s == PB_OK) s = grow((void **)&cnt_inst_, &cap_cnt_inst_, nq_, sizeof(unsigned int), "engine counters");
@@ -775,10 +812,11 @@ void Engine::enqueue_cycle() {
     auto mv = [&](int usel, int k, const int *act) {
         if (timing_ && ev_used_ + 2 <= (int)ev_.size()) cudaEventRecord(ev_[ev_used_], stream_);
         if (W_ > 0) {
+            bmv_plan_kernel<<<1, 256, 0, stream_>>>(d_surf_, nsurf_, act, d_wbase_);
             bmatvec_dispatch(R_, BmvShape{config.T, config.acc},
-                             bmv_args(d_surf_, nsurf_, d_inst_, W_, G_, usel, k, act, part_, cnt_tile_, evals_),
+                             bmv_args(d_surf_, nsurf_, d_inst_, d_wbase_, G_, usel, k, act, part_, cnt_tile_, evals_),
                              (unsigned)G_, stream_, nullptr);
-            ++cycle_kernels_;
+            cycle_kernels_ += 2;
             ++cycle_mv_;
         }
         // single-surface symmetric products; their skip flag is the negated

@@ -48,7 +48,8 @@ struct BSurf {
     float eps, inv_eps, kappa, nk;
     double diag1, diag2;
     int64_t tile_base;     // global index of this surface's first target tile
-    int64_t work_base;     // global index of its first (target tile, source tile) pair
+    int64_t work_base;     // global index of its first (target tile, source tile) pair, all surfaces active
+    int64_t ntiles;        // its target tiles in the batched product (0 for a surface with its own launch)
     int64_t S;             // source tiles
     int inst0;             // first instance
     int nrhs;
@@ -68,12 +69,16 @@ struct BChunk {
     int64_t start;               // relative to the instance's vectors
 };
 
-// Launch arguments of the product (see bmatvec_kernel).
+// Launch arguments of the product (see bmatvec_kernel).  wbase[s] is the
+// first work item of surface s in the split of this launch and wbase[nsurf]
+// the number of work items: bmv_plan_kernel writes them on the device before
+// every launch, giving idle surfaces no work.
 struct BmvArgs {
     const BSurf *surf;
     int nsurf;
     const BInst *inst;
-    int64_t W, G;
+    const int64_t *wbase;
+    int64_t G;
     int usel, k;
     const int *active;
     double *partials;
@@ -150,11 +155,13 @@ __device__ __forceinline__ void ff_add2(float &hi, float &lo, float a, float b) 
 __device__ __forceinline__ int bvol(const int *p) { return *((volatile const int *)p); }
 
 // ---- the multi-surface, multi-right-hand-side product ------------------------
-__device__ __forceinline__ int find_surface(const BSurf *surf, int nsurf, int64_t p) {
+// the surface owning work item p: the last s with wbase[s] <= p (a surface
+// without work shares its base with the next one, which is found instead)
+__device__ __forceinline__ int find_surface(const int64_t *wbase, int nsurf, int64_t p) {
     int lo = 0, hi = nsurf - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (surf[mid].work_base <= p) lo = mid; else hi = mid - 1;
+        if (wbase[mid] <= p) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
@@ -292,7 +299,8 @@ __device__ __forceinline__ void bstage(const float4 *s_g, const float4 *s_w, int
 // thread's 2 R T rows (see BmvRowSums).
 template <int R, int T, int ACCM>
 __global__ void __launch_bounds__(kBThreads)
-bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restrict__ inst, int64_t W, int64_t G,
+bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restrict__ inst,
+               const int64_t *__restrict__ wbase, int64_t G,
                int usel, int k, const int *__restrict__ active, double *__restrict__ partials,
                unsigned int *__restrict__ counters, unsigned long long *__restrict__ evaluated) {
     constexpr int BS = kBThreads, TT = BS * T, TS = kBSourceTile, TQ = TS / 2;
@@ -343,19 +351,26 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
     };
 #define ACC_IDX(w, r, t) ((((w) * R + (r)) * T + (t)))
     const int64_t c = blockIdx.x;
-    int64_t p = sk_begin(c, W, G);
-    const int64_t pend = sk_begin(c + 1, W, G);
+    // this launch's work and grid: every CTA of the split must own at least
+    // one work item (the last-arriver count covers every CTA between a
+    // tile's first and last owner), so with less work than CTAs the surplus
+    // CTAs leave at once
+    const int64_t W = wbase[nsurf];
+    const int64_t Gw = G < W ? G : W;
+    if (c >= Gw) return;
+    int64_t p = sk_begin(c, W, Gw);
+    const int64_t pend = sk_begin(c + 1, W, Gw);
     // global target tile of this CTA's first pair (its partial slot 0)
     int64_t first_tile = -1;
     if (p < pend) {
-        const int s0 = find_surface(surf, nsurf, p);
-        first_tile = surf[s0].tile_base + (p - surf[s0].work_base) / surf[s0].S;
+        const int s0 = find_surface(wbase, nsurf, p);
+        first_tile = surf[s0].tile_base + (p - wbase[s0]) / surf[s0].S;
     }
 
     while (p < pend) {
-        const int si = find_surface(surf, nsurf, p);
+        const int si = find_surface(wbase, nsurf, p);
         const BSurf sf = surf[si];
-        const int64_t local = p - sf.work_base;
+        const int64_t local = p - wbase[si];
         const int64_t S = sf.S;
         const int64_t a = local / S;
         const int64_t s_first = local % S;
@@ -442,8 +457,8 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
                 }
         }
 
-        const int64_t p_tile0 = sf.work_base + a * S;
-        const int64_t c0 = sk_cta_of(p_tile0, W, G), c1 = sk_cta_of(p_tile0 + S - 1, W, G);
+        const int64_t p_tile0 = wbase[si] + a * S;
+        const int64_t c0 = sk_cta_of(p_tile0, W, Gw), c1 = sk_cta_of(p_tile0 + S - 1, W, Gw);
         const int nseg = (int)(c1 - c0 + 1);
         const int64_t gtile = sf.tile_base + a;
         if (nseg == 1) {
@@ -483,9 +498,9 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
                     for (int r = 0; r < R; ++r) { s1[r] = 0.0; s2[r] = 0.0; }
                     for (int o = 0; o < nseg; ++o) {
                         const int64_t co = c0 + o;
-                        const int64_t pb0 = sk_begin(co, W, G);
-                        const int sc = find_surface(surf, nsurf, pb0);
-                        const int64_t ft = surf[sc].tile_base + (pb0 - surf[sc].work_base) / surf[sc].S;
+                        const int64_t pb0 = sk_begin(co, W, Gw);
+                        const int sc = find_surface(wbase, nsurf, pb0);
+                        const int64_t ft = surf[sc].tile_base + (pb0 - wbase[sc]) / surf[sc].S;
                         const double *pp = partials + (2 * co + (gtile == ft ? 0 : 1)) * (2 * R * TT);
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
@@ -516,7 +531,7 @@ bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restric
 template <int R, int T, int ACCM>
 cudaError_t bmv_launch_or_query(const BmvArgs &a, unsigned grid, cudaStream_t s, int *occ) {
     if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bmatvec_kernel<R, T, ACCM>, kBThreads, 0);
-    bmatvec_kernel<R, T, ACCM><<<grid, kBThreads, 0, s>>>(a.surf, a.nsurf, a.inst, a.W, a.G, a.usel, a.k, a.active,
+    bmatvec_kernel<R, T, ACCM><<<grid, kBThreads, 0, s>>>(a.surf, a.nsurf, a.inst, a.wbase, a.G, a.usel, a.k, a.active,
                                                            a.partials, a.counters, a.evaluated);
     return cudaSuccess;
 }

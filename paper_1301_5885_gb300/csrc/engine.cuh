@@ -106,6 +106,8 @@ class Engine {
     std::vector<int> surf_member_;     // table surface -> member index
     std::vector<int> direct_;          // table surfaces with their own symmetric product
     BSurf *d_surf_ = nullptr;
+    int64_t *d_wbase_ = nullptr;       // the work split of the current product (bmv_plan_kernel)
+    size_t cap_wbase_ = 0;
     BInst *d_inst_ = nullptr;
     BChunk *d_ch_ = nullptr;
     unsigned int *cnt_inst_ = nullptr, *cnt_tile_ = nullptr;
