@@ -771,31 +771,44 @@ def run_serve(args):
     gaps = rng.exponential(1.0 / rate, size=args.requests)
     picks = rng.integers(0, len(pool), size=args.requests)
     kaps = rng.integers(0, 2, size=args.requests)
+    def stream(split_n, sampler=None):
+        """The Poisson stream through a server; returns (results, wall s,
+        stats before, stats after, launches, request keys)."""
+        with pb.Server(max_active=16, hbm_budget_bytes=budget, tol=args.tol, split_n=split_n) as sv:
+            st0 = sv.stats()
+            if sampler:
+                sampler.start()
+            l0 = pb.pb_kernel_launches()
+            t_start = time.perf_counter()
+            keys_by_id = {}
+
+            def feeder():
+                for g, k, kk in zip(gaps, picks, kaps):
+                    time.sleep(float(g))
+                    keys_by_id[submit(sv, int(k), kappas[int(kk)])] = (int(k), int(kk))
+            th = threading.Thread(target=feeder)
+            th.start()
+            th.join()
+            sv.wait(args.requests, 3600.0)
+            t_end = time.perf_counter()
+            out = sv.poll(4096)
+            st = sv.stats()
+            return out, t_end - t_start, st0, st, pb.pb_kernel_launches() - l0, keys_by_id
+
     sampler = _clock_and_uuid(torch, dev)
-    with pb.Server(max_active=16, hbm_budget_bytes=budget, tol=args.tol) as sv:
-        st0 = sv.stats()
-        sampler.start()
-        l0 = pb.pb_kernel_launches()
-        t_start = time.perf_counter()
+    res, wall, st0, st1, launches, req_key = stream(0, sampler)
+    clocks = sampler.stop()
+    res1, wall1, _, _, _, _ = stream(-1)
 
-        req_key = {}
-
-        def feeder():
-            for g, k, kk in zip(gaps, picks, kaps):
-                time.sleep(float(g))
-                req_key[submit(sv, int(k), kappas[int(kk)])] = (int(k), int(kk))
-        th = threading.Thread(target=feeder)
-        th.start()
-        th.join()
-        sv.wait(args.requests, 3600.0)
-        t_end = time.perf_counter()
-        res = sv.poll(4096)
-        st1 = sv.stats()
-        launches = pb.pb_kernel_launches() - l0
-        clocks = sampler.stop()
+    def lat_split(rs):
+        small = np.array([r["latency_ms"] for r in rs if r["n"] < 16384])
+        large = np.array([r["latency_ms"] for r in rs if r["n"] >= 16384])
+        f = lambda a, q: float(np.percentile(a, q)) if a.size else None
+        return {"small_p50": f(small, 50), "small_p99": f(small, 99), "large_p50": f(large, 50),
+                "large_p99": f(large, 99), "n_small": int(small.size), "n_large": int(large.size)}
     lat = np.array([r["latency_ms"] for r in res])
-    ok = all(r["status"] == pb.PB_OK for r in res)
-    wall = t_end - t_start
+    lat1 = np.array([r["latency_ms"] for r in res1])
+    ok = all(r["status"] == pb.PB_OK for r in res) and all(r["status"] == pb.PB_OK for r in res1)
     products = st1["pair_products"] - st0["pair_products"]
     # one-at-a-time baselines on the same request mix, from per-item solve
     # times: every distinct (solute, kappa) of the stream solved alone in FP32
@@ -866,8 +879,13 @@ def run_serve(args):
                        "distinct_requests": len(keys), "max_active": 16, "hbm_budget_bytes": budget,
                        "gmres_tol": args.tol, "l2": "inputs exceed L2 across the stream; no flush"},
             "solves_per_s": len(res) / wall,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "mean": float(lat.mean())},
+            "latency_ms": dict({"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                "mean": float(lat.mean())}, **lat_split(res)),
+            "one_lane": {"note": "the same stream through a server with one lane (split_n = -1): every request "
+                                 "in one lockstep engine",
+                         "solves_per_s": len(res1) / wall1,
+                         "latency_ms": dict({"p50": float(np.percentile(lat1, 50)),
+                                             "p99": float(np.percentile(lat1, 99))}, **lat_split(res1))},
             "all_converged": ok, "max_active_seen": st1["max_active_seen"],
             "rel_energy_err": {"max_vs_oracle": max(errs) if errs else None, "results_compared": len(errs),
                                "note": "against the stored FP64 oracle solutions (tests/golden) of the pool "

@@ -279,7 +279,14 @@ int pb_batch_shapes(int rhs_width, int *targets_per_thread, int *row_sums, int m
  * queued) are collected with pb_server_poll; pb_server_wait blocks until at
  * least n results are waiting or the timeout passes (PB_ERR_TIMEOUT).
  * pb_server_destroy drops requests not yet admitted, finishes the running
- * ones, and frees everything. */
+ * ones, and frees everything.
+ * Two lanes (split_n >= 0): requests with N < split_n (whose products share
+ * one batched launch) and the others (each with its own symmetric product)
+ * run on two worker threads and streams, the small lane's with the higher
+ * priority; max_active applies per lane and the budget to both together.
+ * While small requests run, the large lane's products use one CTA per SM
+ * fewer than their occupancy, which leaves the small lane's kernels room to
+ * run at the same time. */
 typedef struct pb_server pb_server;
 typedef struct {
     int max_active;           /* running requests at most (8 if <= 0) */
@@ -287,6 +294,7 @@ typedef struct {
     int restart;              /* GMRES restart (10 if <= 0) */
     double tol;               /* relative residual (1e-4 if <= 0) */
     int maxit;                /* Arnoldi steps per request (1000 if <= 0) */
+    int64_t split_n;          /* requests with N >= split_n go to the large lane (16,384 if 0; < 0: one lane) */
 } pb_server_opts;
 typedef struct {
     uint64_t id;

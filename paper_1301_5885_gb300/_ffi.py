@@ -51,7 +51,7 @@ class _BatchInfo(ctypes.Structure):
 
 class _ServerOpts(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64), ("restart", ctypes.c_int),
-                ("tol", ctypes.c_double), ("maxit", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("split_n", ctypes.c_int64)]
 
 
 class _ServerResult(ctypes.Structure):
@@ -513,8 +513,10 @@ class Server:
     """A solve server with continuous batching (pb_server_* of include/pb.h)."""
 
     def __init__(self, max_active: int = 8, hbm_budget_bytes: int = 8 << 30, restart: int = 10,
-                 tol: float = 1e-4, maxit: int = 1000):
-        o = _ServerOpts(int(max_active), int(hbm_budget_bytes), int(restart), float(tol), int(maxit))
+                 tol: float = 1e-4, maxit: int = 1000, split_n: int = 0):
+        """split_n: requests with N >= split_n take the large lane (0: the
+        library's default, 16,384; negative: one lane for all requests)."""
+        o = _ServerOpts(int(max_active), int(hbm_budget_bytes), int(restart), float(tol), int(maxit), int(split_n))
         h = ctypes.c_void_p()
         _check(lib().pb_server_create(ctypes.byref(o), ctypes.byref(h)))
         self.handle = h.value

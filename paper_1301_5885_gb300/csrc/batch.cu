@@ -715,7 +715,8 @@ pb_status Engine::rebuild() {
     retile(hs, direct_flag, TT, &tiles, &work);
     tiles_ = tiles;
     W_ = work;
-    const int cps = (config.ctas_per_sm > 0 && config.ctas_per_sm < occ) ? config.ctas_per_sm : occ;
+    int cps = (config.ctas_per_sm > 0 && config.ctas_per_sm < occ) ? config.ctas_per_sm : occ;
+    if (cta_cap_ > 0 && cps > cta_cap_) cps = cta_cap_;
     G_ = (int64_t)num_sms_ * cps;
     if (G_ > W_) G_ = W_;
     ctas = G_;
@@ -798,7 +799,11 @@ pb_status Engine::rebuild() {
     occ = 1;
     e = bmatvec_dispatch(R_, BmvShape{config.T, config.acc}, BmvArgs{}, 0, stream_, &occ);
     if (e != cudaSuccess) return cuda_fail(e, "engine: batched product shape");
-    G_ = (int64_t)num_sms_ * ((config.ctas_per_sm > 0 && config.ctas_per_sm < occ) ? config.ctas_per_sm : occ);
+    {
+        int cps2 = (config.ctas_per_sm > 0 && config.ctas_per_sm < occ) ? config.ctas_per_sm : occ;
+        if (cta_cap_ > 0 && cps2 > cta_cap_) cps2 = cta_cap_;
+        G_ = (int64_t)num_sms_ * cps2;
+    }
     if (G_ > W_) G_ = W_;
     ctas = G_;
     e = cudaMemcpyAsync(d_surf_, hs.data(), nsurf_ * sizeof(BSurf), cudaMemcpyHostToDevice, stream_);

@@ -62,6 +62,14 @@ class Engine {
     // time_products (no graph), the product launches are bracketed by CUDA
     // events and their time is added to matvec_ms.
     pb_status cycle(bool use_graph, bool time_products = false);
+    // Caps the batched product's CTAs per SM (0: no cap); takes effect at the
+    // next cycle (the tables are rebuilt).
+    void set_cta_cap(int cap) {
+        if (cap != cta_cap_) {
+            cta_cap_ = cap;
+            dirty_ = true;
+        }
+    }
     // Eq. (14) for every instance of a member (float-float pairs), kcal/mol.
     pb_status energies(EngineMember *m, double *out);
     // Bytes one member of N triangles with nrhs sets needs (vectors and states).
@@ -122,6 +130,7 @@ class Engine {
     cudaGraph_t graph_ = nullptr;
     int kernels_per_cycle_ = 0, mv_per_cycle_ = 0, cycle_kernels_ = 0, cycle_mv_ = 0;
     bool timing_ = false;
+    int cta_cap_ = 0;            // CTAs per SM of the batched product at most (0: none)
     BmvConfig kept_;             // an autotuning engine's choice, kept across rebuilds
     int kept_R_ = 0;
     std::vector<cudaEvent_t> ev_;

@@ -1,20 +1,29 @@
 // server.cu -- a solve server with continuous batching.
 //
 // Clients submit PB solve requests (a surface, a charge set and the physical
-// constants) from any thread; a worker thread owns the GPU stream and runs the
-// lockstep engine of batch.cu.  Between two restart cycles the worker
-//   - finishes every request whose instance has converged (or failed): energy
-//     (Eq. (14)), result with its latency, and release of its device memory;
-//   - admits queued requests in arrival order while the number of active
-//     requests is below the slot limit and their estimated device footprint
-//     fits the memory budget (a request larger than the whole budget is
-//     rejected with PB_ERR_ADMIT);
+// constants) from any thread.  Requests go to one of two lanes by size: small
+// surfaces (N < split_n), whose products share one batched launch, and large
+// ones, each with its own symmetric product.  Each lane has a worker thread,
+// a CUDA stream and the lockstep engine of batch.cu; the small lane's stream
+// has the higher priority.  Between two restart cycles a worker
+//   - finishes every request of its lane whose instance has converged (or
+//     failed): energy (Eq. (14)), result with its latency, and release of its
+//     device memory;
+//   - admits its lane's queued requests in arrival order while the lane has
+//     fewer than max_active running and their estimated device footprint fits
+//     the memory budget shared by both lanes (a request larger than the whole
+//     budget is rejected with PB_ERR_ADMIT);
 // so requests that arrive while others are on the GPU join the running batch
 // at the next cycle boundary and their products share the same launches.
-// Every wait is bounded; no request ever waits on the GPU with a lock held.
+// A large request's product fills every SM with persistent CTAs; while small
+// requests are running, the large lane launches its products with one CTA
+// per SM fewer, so that the small lane's kernels find free slots and its
+// requests are not held to the large products' step time.  Every wait is
+// bounded; no request ever waits on the GPU with a lock held.
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -30,6 +39,7 @@ using namespace pb;
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr int64_t kDefaultSplitN = 16384;   // from here a context's product is the symmetric one
 
 struct Request {
     uint64_t id = 0;
@@ -40,6 +50,17 @@ struct Request {
     int64_t bytes = 0;
     pb_ctx *ctx = nullptr;
     EngineMember *member = nullptr;
+    int cps = 0;                  // CTAs per SM its symmetric product is configured with (0: occupancy)
+};
+
+struct Lane {
+    int index = 0;
+    cudaStream_t stream = nullptr;
+    Engine *eng = nullptr;
+    std::thread worker;
+    std::deque<Request *> pending;
+    std::vector<Request *> active;
+    std::atomic<int> n_active{0};
 };
 
 }  // namespace
@@ -48,18 +69,17 @@ struct pb_server {
     pb_server_opts opts{};
     int device = 0;
     int num_sms = 0;
-    cudaStream_t stream = nullptr;
-    Engine *eng = nullptr;
-    std::thread worker;
+    int nlanes = 2;
+    int64_t split_n = kDefaultSplitN;
+    Lane lanes[2];
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<Request *> pending;
-    std::vector<Request *> active;
     std::deque<pb_server_result> done;
     bool stop = false;
     uint64_t next_id = 1;
     int64_t used_bytes = 0;
     pb_server_stats stats{};
+    int64_t lane_evals[2] = {0, 0}, lane_products[2] = {0, 0};
     Clock::time_point t0;
 };
 
@@ -77,7 +97,7 @@ int64_t footprint(int64_t N, int64_t Nc, int m, int num_sms) {
     return ctx_bytes + default_scratch_bytes(N, num_sms) + Engine::member_bytes(N, 1, m) + Nc * 32;
 }
 
-void finish(pb_server *sv, Request *r, int status, double energy, int iters) {
+void finish(pb_server *sv, Lane &L, Request *r, int status, double energy, int iters) {
     pb_server_result res;
     memset(&res, 0, sizeof(res));
     res.id = r->id;
@@ -89,7 +109,7 @@ void finish(pb_server *sv, Request *r, int status, double energy, int iters) {
     res.latency_ms = ms_between(r->t_submit, now);
     res.queue_ms = r->member ? ms_between(r->t_submit, r->t_admit) : res.latency_ms;
     if (r->member) {
-        sv->eng->remove(r->member);
+        L.eng->remove(r->member);
         r->member = nullptr;
     }
     if (r->ctx) {
@@ -105,38 +125,38 @@ void finish(pb_server *sv, Request *r, int status, double energy, int iters) {
     delete r;
 }
 
-// Admit queued requests that fit; runs on the worker thread.
-void admit(pb_server *sv) {
+// Admit a lane's queued requests that fit; runs on the lane's worker.
+void admit(pb_server *sv, Lane &L) {
     for (;;) {
         Request *r = nullptr;
         bool too_big = false;
         {
             std::lock_guard<std::mutex> lock(sv->mu);
-            if (sv->pending.empty() || (int)sv->active.size() >= sv->opts.max_active) return;
-            Request *head = sv->pending.front();
+            if (L.pending.empty() || (int)L.active.size() >= sv->opts.max_active) return;
+            Request *head = L.pending.front();
             too_big = head->bytes > sv->opts.hbm_budget_bytes;
             if (!too_big && sv->used_bytes + head->bytes > sv->opts.hbm_budget_bytes) return;   // wait for memory
-            sv->pending.pop_front();
+            L.pending.pop_front();
             r = head;
             sv->used_bytes += r->bytes;            // released by finish()
             if (too_big) sv->stats.rejected += 1;
             else sv->stats.admitted += 1;
         }
         if (too_big) {
-            finish(sv, r, PB_ERR_ADMIT, 0.0, 0);
+            finish(sv, L, r, PB_ERR_ADMIT, 0.0, 0);
             continue;
         }
         r->t_admit = Clock::now();
         pb_status s = pb_create(r->c.data(), r->n.data(), r->a.data(), r->N, r->Nc > 0 ? r->q.data() : nullptr, r->Nc,
-                                r->eps1, r->eps2, r->kappa, sv->stream, &r->ctx);
+                                r->eps1, r->eps2, r->kappa, L.stream, &r->ctx);
         if (s != PB_OK) {
-            finish(sv, r, s, 0.0, 0);
+            finish(sv, L, r, s, 0.0, 0);
             continue;
         }
-        r->member = sv->eng->add(r->ctx, r->q.data(), r->Nc, 1, r->id, &s);
+        r->member = L.eng->add(r->ctx, r->q.data(), r->Nc, 1, r->id, &s);
         if (s != PB_OK || !r->member) {
             r->member = nullptr;
-            finish(sv, r, s == PB_OK ? PB_ERR_CUDA : s, 0.0, 0);
+            finish(sv, L, r, s == PB_OK ? PB_ERR_CUDA : s, 0.0, 0);
             continue;
         }
         // the context now holds the geometry: drop the host copies
@@ -144,34 +164,61 @@ void admit(pb_server *sv) {
         std::vector<double>().swap(r->n);
         std::vector<double>().swap(r->a);
         std::lock_guard<std::mutex> lock(sv->mu);
-        sv->active.push_back(r);
+        L.active.push_back(r);
+        L.n_active.store((int)L.active.size());
     }
 }
 
-void worker_main(pb_server *sv) {
+// Large lane: while the small lane runs requests, symmetric products use one
+// CTA per SM fewer than their occupancy (so small-lane kernels find slots).
+pb_status set_yield(Lane &L, bool yield) {
+    for (Request *r : L.active) {
+        pb_ctx *c = r->ctx;
+        if (!c || !f32_variant_symmetric(c->f32_variant)) continue;
+        const int occ = matvec_f32_occupancy(c->f32_variant);
+        const int want = (yield && occ > 1) ? occ - 1 : 0;
+        if (want == r->cps) continue;
+        pb_status s = matvec_configure(c, c->f32_variant, want);
+        if (s == PB_OK) s = matvec_prepare(c);
+        if (s != PB_OK) return s;
+        r->cps = want;
+    }
+    return PB_OK;
+}
+
+void worker_main(pb_server *sv, int li) {
     cudaSetDevice(sv->device);
+    Lane &L = sv->lanes[li];
+    Lane *other = (sv->nlanes == 2) ? &sv->lanes[1 - li] : nullptr;
     for (;;) {
         {
             std::unique_lock<std::mutex> lock(sv->mu);
-            if (sv->stop && sv->pending.empty() && sv->active.empty()) break;
-            if (sv->active.empty() && sv->pending.empty())
-                sv->cv.wait_for(lock, std::chrono::milliseconds(2));
+            if (sv->stop && L.pending.empty() && L.active.empty()) break;
+            if (L.active.empty() && L.pending.empty()) sv->cv.wait_for(lock, std::chrono::milliseconds(2));
         }
-        admit(sv);
+        admit(sv, L);
         std::vector<Request *> act;
         {
             std::lock_guard<std::mutex> lock(sv->mu);
-            act = sv->active;
+            act = L.active;
         }
         if (act.empty()) continue;
-        pb_status s = sv->eng->cycle(false);
+        pb_status s = PB_OK;
+        // the two lanes share the SMs while both run: the large lane's
+        // symmetric products leave one CTA slot per SM, the small lane's
+        // batched product uses one CTA per SM (so it fits in those slots)
+        if (li == 1 && other) s = set_yield(L, other->n_active.load() > 0);
+        if (li == 0 && other) L.eng->set_cta_cap(other->n_active.load() > 0 ? 1 : 0);
+        if (s == PB_OK) s = L.eng->cycle(false);
         {
             std::lock_guard<std::mutex> lock(sv->mu);
             sv->stats.cycles += 1;
-            sv->stats.pair_evals = sv->eng->pair_evals;
-            sv->stats.pair_products = sv->eng->pair_products;
-            sv->stats.max_active_seen = (int)act.size() > sv->stats.max_active_seen ? (int)act.size()
-                                                                                     : sv->stats.max_active_seen;
+            sv->lane_evals[li] = L.eng->pair_evals;
+            sv->lane_products[li] = L.eng->pair_products;
+            sv->stats.pair_evals = sv->lane_evals[0] + sv->lane_evals[1];
+            sv->stats.pair_products = sv->lane_products[0] + sv->lane_products[1];
+            const int total = (int)(sv->lanes[0].active.size() + (sv->nlanes == 2 ? sv->lanes[1].active.size() : 0));
+            if (total > sv->stats.max_active_seen) sv->stats.max_active_seen = total;
         }
         for (Request *r : act) {
             bool fin = (s != PB_OK) || r->member->finished;
@@ -183,18 +230,19 @@ void worker_main(pb_server *sv) {
                 st = r->member->status[0].converged ? PB_OK
                                                     : (r->member->status[0].status == PB_OK ? PB_ERR_NOCONV
                                                                                             : r->member->status[0].status);
-                pb_status es = sv->eng->energies(r->member, &e);
+                pb_status es = L.eng->energies(r->member, &e);
                 if (es != PB_OK) st = es;
             }
             {
                 std::lock_guard<std::mutex> lock(sv->mu);
-                for (size_t i = 0; i < sv->active.size(); ++i)
-                    if (sv->active[i] == r) {
-                        sv->active.erase(sv->active.begin() + i);
+                for (size_t i = 0; i < L.active.size(); ++i)
+                    if (L.active[i] == r) {
+                        L.active.erase(L.active.begin() + i);
                         break;
                     }
+                L.n_active.store((int)L.active.size());
             }
-            finish(sv, r, st, e, it);
+            finish(sv, L, r, st, e, it);
         }
     }
 }
@@ -206,7 +254,7 @@ extern "C" {
 pb_status pb_server_create(const pb_server_opts *opts, pb_server **out) {
     if (!out) return set_error(nullptr, PB_ERR_ARG, "pb_server_create: out is NULL");
     *out = nullptr;
-    pb_server_opts o{8, (int64_t)8 << 30, 10, 1e-4, 1000};
+    pb_server_opts o{8, (int64_t)8 << 30, 10, 1e-4, 1000, 0};
     if (opts) {
         o = *opts;
         if (o.max_active <= 0) o.max_active = 8;
@@ -218,16 +266,26 @@ pb_status pb_server_create(const pb_server_opts *opts, pb_server **out) {
     if (o.restart > kMaxRestart) return set_error(nullptr, PB_ERR_ARG, "pb_server_create: restart > %d", kMaxRestart);
     pb_server *sv = new pb_server();
     sv->opts = o;
+    sv->nlanes = o.split_n < 0 ? 1 : 2;
+    sv->split_n = o.split_n > 0 ? o.split_n : kDefaultSplitN;
+    int lo = 0, hi = 0;
     cudaError_t e = cudaGetDevice(&sv->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, sv->device);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);   // hi: the highest priority
+    for (int li = 0; li < sv->nlanes && e == cudaSuccess; ++li)
+        e = cudaStreamCreateWithPriority(&sv->lanes[li].stream, cudaStreamNonBlocking, li == 0 ? hi : lo);
     if (e != cudaSuccess) {
+        for (int li = 0; li < 2; ++li)
+            if (sv->lanes[li].stream) cudaStreamDestroy(sv->lanes[li].stream);
         delete sv;
         return cuda_error(nullptr, e, "pb_server_create");
     }
-    sv->eng = new Engine(sv->stream, sv->device, sv->num_sms, o.restart, o.tol, o.maxit);
+    for (int li = 0; li < sv->nlanes; ++li) {
+        sv->lanes[li].index = li;
+        sv->lanes[li].eng = new Engine(sv->lanes[li].stream, sv->device, sv->num_sms, o.restart, o.tol, o.maxit);
+    }
     sv->t0 = Clock::now();
-    sv->worker = std::thread(worker_main, sv);
+    for (int li = 0; li < sv->nlanes; ++li) sv->lanes[li].worker = std::thread(worker_main, sv, li);
     *out = sv;
     return PB_OK;
 }
@@ -258,7 +316,7 @@ pb_status pb_server_submit(pb_server *sv, const double *centroids, const double 
             return set_error(nullptr, PB_ERR_ARG, "pb_server_submit: server is shutting down");
         }
         r->id = sv->next_id++;
-        sv->pending.push_back(r);
+        sv->lanes[(sv->nlanes == 2 && N >= sv->split_n) ? 1 : 0].pending.push_back(r);
         sv->stats.submitted += 1;
         if (id) *id = r->id;
     }
@@ -294,8 +352,12 @@ pb_status pb_server_get_stats(pb_server *sv, pb_server_stats *out) {
     if (!sv || !out) return set_error(nullptr, PB_ERR_ARG, "pb_server_get_stats: NULL argument");
     std::lock_guard<std::mutex> lock(sv->mu);
     *out = sv->stats;
-    out->active = (int)sv->active.size();
-    out->pending = (int)sv->pending.size();
+    out->active = 0;
+    out->pending = 0;
+    for (int li = 0; li < sv->nlanes; ++li) {
+        out->active += (int)sv->lanes[li].active.size();
+        out->pending += (int)sv->lanes[li].pending.size();
+    }
     out->used_bytes = sv->used_bytes;
     return PB_OK;
 }
@@ -306,15 +368,20 @@ void pb_server_destroy(pb_server *sv) {
         std::lock_guard<std::mutex> lock(sv->mu);
         sv->stop = true;
         // drop requests that were never admitted
-        while (!sv->pending.empty()) {
-            delete sv->pending.front();
-            sv->pending.pop_front();
+        for (int li = 0; li < sv->nlanes; ++li) {
+            while (!sv->lanes[li].pending.empty()) {
+                delete sv->lanes[li].pending.front();
+                sv->lanes[li].pending.pop_front();
+            }
         }
     }
     sv->cv.notify_all();
-    if (sv->worker.joinable()) sv->worker.join();   // finishes the active requests
-    delete sv->eng;
-    cudaStreamDestroy(sv->stream);
+    for (int li = 0; li < sv->nlanes; ++li)
+        if (sv->lanes[li].worker.joinable()) sv->lanes[li].worker.join();   // finishes the active requests
+    for (int li = 0; li < sv->nlanes; ++li) {
+        delete sv->lanes[li].eng;
+        cudaStreamDestroy(sv->lanes[li].stream);
+    }
     delete sv;
 }
 
