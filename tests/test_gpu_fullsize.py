@@ -86,10 +86,14 @@ def _sampled_rows(p, nrows, seed):
     return u, rows, r1, r2
 
 
-@pytest.mark.parametrize("which", ["sphere2", "protein300k"])
+@pytest.mark.parametrize("which", ["sphere2", "sphere2_salt_free", "protein300k"])
 def test_sampled_rows_at_full_size(which, sphere2):
+    """Sampled rows (first and last included) of the products the benchmark
+    times, at full size: the 81,920-triangle sphere with and without salt
+    (the kappa = 0 symmetric kernel) and the 300,176-triangle solute."""
     pb = _pb()
-    p = sphere2 if which == "sphere2" else pi.protein_like()
+    p = {"sphere2": lambda: sphere2, "sphere2_salt_free": lambda: pi.by_name("sphere2_salt_free"),
+         "protein300k": lambda: pi.protein_like()}[which]()
     assert p.n > 80_000
     u, rows, r1, r2 = _sampled_rows(p, 96, seed=21)
     with _ctx(p) as ctx:
