@@ -141,3 +141,23 @@ def test_wait_is_bounded():
             sv.wait(1, 0.2)
         assert ei.value.status == pb.PB_ERR_TIMEOUT
         assert time.time() - t < 5.0
+
+
+def test_two_lanes_and_one_lane_give_the_same_results():
+    """The default server splits requests into a small and a large lane by N
+    (two workers and streams; the large lane's products run with one CTA per
+    SM fewer while small requests run).  The same requests through a
+    one-lane server (split_n < 0) give the same energies (1e-6), and so does
+    a split that puts every request in the large lane."""
+    pb = _pb()
+    reqs = _requests()
+    out = {}
+    for split in (0, -1, 1):
+        with pb.Server(max_active=8, tol=1e-7, split_n=split) as sv:
+            ids = [_submit(sv, p) for p in reqs]
+            got = _collect(sv, len(reqs))
+        assert all(got[i]["status"] == pb.PB_OK for i in ids)
+        out[split] = [got[i]["energy_kcal"] for i in ids]
+    for a, b, c in zip(out[0], out[-1], out[1]):
+        assert a == pytest.approx(b, rel=1e-6)
+        assert a == pytest.approx(c, rel=1e-6)
