@@ -51,11 +51,11 @@ UNIT = "Gpairs/s"
 # both rows, so k is half their per-pair count.
 SMS = 152
 SM_MAX_MHZ = 2070.0
-# The hot-path scope's own work count for one ordered pair of the product
+# The work count of one ordered pair of the product evaluated on its own
 # (kappa > 0): 45 FP32 operations evaluating K1..K4 for that pair alone.  The
 # symmetric kernels do less per ordered pair, because one evaluation of an
 # unordered pair serves both rows; their fraction on this basis can exceed 1.
-SURVEY_OPS_PER_PAIR = 45
+ORDERED_PAIR_OPS = 45
 MATVEC_KERNELS = {
     1: ("matvec_f32_kernel", 41, 41),
     2: ("matvec_f32x2_kernel<2>", 39, 18),
@@ -359,10 +359,10 @@ class SolveLeg:
                               "SM clock; not a measured peak)") if ops else "FP64 pipe",
                "avg_launch_ms": avg_ms, "launches": mv_n, "share_of_step": mv_ms / total_ms}
         if self.args.prec == "fp32pair" and self.prob.kappa > 0.0:
-            speak = matvec_peak_gpairs(SURVEY_OPS_PER_PAIR)
-            out["survey_basis"] = {
+            speak = matvec_peak_gpairs(ORDERED_PAIR_OPS)
+            out["ordered_pair_basis"] = {
                 "peak": speak, "frac": achieved / speak,
-                "basis": f"{SURVEY_OPS_PER_PAIR} FP32 ops per ordered pair (K1..K4 evaluated for every ordered "
+                "basis": f"{ORDERED_PAIR_OPS} FP32 ops per ordered pair (K1..K4 evaluated for every ordered "
                          "pair); the symmetric kernel evaluates each unordered pair once for both rows, so it "
                          "exceeds 1 on this basis"}
         return out
