@@ -687,14 +687,15 @@ def run_batch(args):
         # product kernel timing (one extra batch, kernels launched one by one with events)
         _, tinfo = pb.pb_batch_solve(ctxs, variants, restart=args.restart, tol=args.tol, use_graph="timed",
                                      raise_on_noconv=False)
-        # accuracy: the smallest surfaces, every charge set, against FP64 GPU solves at tol 1e-10
-        small = sorted(range(len(ctxs)), key=lambda i: ns[i])[:4]
+        # accuracy: every charge set of the surfaces with a stored FP64 oracle
+        # solution (the four smallest; tests/golden), against that solution
         errs = []
-        for i in small:
+        for i in range(len(ctxs)):
             for r in range(8):
-                pb.pb_set_charges(ctxs[i], variants[i][r])
-                e64 = pb.pb_solve(ctxs[i], restart=10, tol=1e-10, maxit=3000, prec="fp64").energy_kcal
-                errs.append(abs(energies[i][r] - e64) / abs(e64))
+                name = f"batch{i}_set{r}"
+                ref = golden_energy(name)
+                if ref is not None and golden_n(name) == ns[i]:
+                    errs.append(abs(energies[i][r] - ref) / abs(ref))
         for c in ctxs:
             pb.pb_destroy(c)
     total_ms = sum(times)
@@ -720,7 +721,9 @@ def run_batch(args):
                        "l2": "flushed between steps (256 MiB write)"},
             "solves_per_s": nsolve / (total_ms * 1e-3),
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
-            "rel_energy_err": {"max_vs_fp64_gpu_smallest4x8": max(errs)},
+            "rel_energy_err": {"max_vs_oracle": max(errs) if errs else None, "results_compared": len(errs),
+                               "note": "against the stored FP64 oracle solutions (tests/golden) of the four "
+                                       "smallest solutes, all 8 charge sets"},
             "gmres": {"iters_max": infos[-1]["iters_max"], "cycles": infos[-1]["cycles"],
                       "converged": f"{infos[-1]['converged']}/{infos[-1]['instances']}"},
             "phases_ms": {"setup": infos[-1]["setup_ms"], "cycles": infos[-1]["cycles_ms"],

@@ -211,10 +211,23 @@ def solute_from_spec(spec, kappa: float = KAPPA) -> Problem:
     return Problem(p.name, p.surface, p.charges, kappa=kappa)
 
 
+def batch_problem(k: int, r: int) -> Problem:
+    """Solute k of the 64-solute batch with its charge variant r (of 8; the
+    variants drawn with seed 3000 + k)."""
+    from .charges import charge_variants
+    p = solute_from_spec(batch_specs(64)[k])
+    q = charge_variants(p.charges, 8, seed=3000 + k)[r]
+    return Problem(f"{p.name}_set{r}", p.surface, q, p.eps1, p.eps2, p.kappa)
+
+
 def by_name(name: str) -> Problem:
     """The named synthetic workloads used by the tests and the benchmark.
     ``serve<k>_kappa<0|1>``: solute k of the 64-solute serving pool with
-    kappa 0 or 0.1257."""
+    kappa 0 or 0.1257; ``batch<k>_set<r>``: solute k of the 64-solute batch
+    with charge variant r."""
+    if name.startswith("batch") and "_set" in name:
+        k, r = name[len("batch"):].split("_set")
+        return batch_problem(int(k), int(r))
     if name.startswith("serve") and "_kappa" in name:
         k, kap = name[len("serve"):].split("_kappa")
         return solute_from_spec(serve_specs(64)[int(k)], kappa=(0.0 if kap == "0" else KAPPA))
