@@ -8,9 +8,10 @@ repository root:
     python tests/golden/make_golden.py [--tol T] [--checkpoint FILE] [name ...]
 
 ``--checkpoint FILE`` saves the GMRES iterate at every restart (an .npz) and,
-when FILE already exists for the same workload and tolerance, resumes from it:
-GMRES(m) restarts from its current approximation anyway, so a resumed run
-takes exactly the steps the uninterrupted one would.  This lets the
+when FILE already exists for the same workload, resumes from it: GMRES(m)
+restarts from its current approximation anyway, so a resumed run with the
+same settings takes exactly the steps the uninterrupted one would (and one
+with another tolerance or restart length continues from the same iterate).  This lets the
 300,000-triangle solve (hours of oracle time) survive an interruption.
 
 Each entry records the surface's size, total area and centroid sum, so that a
@@ -48,8 +49,11 @@ def run(name: str, tol: float, checkpoint: str | None, maxit: int, restart: int 
     if checkpoint and os.path.exists(checkpoint):
         ck = np.load(checkpoint)
         keys = set(ck.files)
-        if ({"name", "tol", "restart", "x", "iters", "seconds", "resid"} <= keys and str(ck["name"]) == name
-                and float(ck["tol"]) == tol and int(ck["restart"]) == restart and ck["x"].shape == (2 * p.n,)):
+        # restarted GMRES continues from its current approximation, so a
+        # saved iterate is a valid start whatever tolerance or restart length
+        # the run that wrote it used
+        if ({"name", "x", "iters", "seconds", "resid"} <= keys and str(ck["name"]) == name
+                and ck["x"].shape == (2 * p.n,)):
             x0, it0, sec0 = ck["x"], int(ck["iters"]), float(ck["seconds"])
             print(f"{name}: resuming at iteration {it0}, rel. residual {float(ck['resid']):.3e}", flush=True)
     t = time.time()
