@@ -131,6 +131,9 @@ def parse():
                          "row-sharded over the job's GPUs (strong scaling, launch with torchrun for N > 1)")
     ap.add_argument("--variant", type=int, default=0,
                     help="matvec mode: FP32-pair kernel variant (0: the library's default for N)")
+    ap.add_argument("--scratch-mb", type=float, default=0.0,
+                    help="solve/matvec modes: bound on the symmetric product's scratch in MiB "
+                         "(0: none; bounded, the product runs in bands of row tiles)")
     ap.add_argument("--n-solutes", type=int, default=64, help="batch mode: solutes per batch")
     ap.add_argument("--frames", type=int, default=20, help="frames mode: trajectory length")
     ap.add_argument("--batch-shape", default=None,
@@ -275,9 +278,12 @@ def run_reference(args):
 
 
 def config_dict(args, prob):
-    return {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_triangles": prob.n,
-            "n_charges": prob.nc, "precision": args.prec, "gmres_restart": args.restart, "gmres_tol": args.tol,
-            "l2": "flushed between steps (256 MiB write)"}
+    d = {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_triangles": prob.n,
+         "n_charges": prob.nc, "precision": args.prec, "gmres_restart": args.restart, "gmres_tol": args.tol,
+         "l2": "flushed between steps (256 MiB write)"}
+    if getattr(args, "scratch_mb", 0):
+        d["scratch_bound_mib"] = args.scratch_mb
+    return d
 
 
 def reduce_over_ranks(total_ms: float, pairs: float, solves: float, device, dist=None):
@@ -308,6 +314,8 @@ class SolveLeg:
         pb, prob, args = self.pb, self.prob, self.args
         ctx = pb.pb_create(c, nr, a, q, prob.eps1, prob.eps2, prob.kappa, stream=self.stream)
         try:
+            if args.scratch_mb:
+                pb.pb_set_scratch_limit(ctx, int(args.scratch_mb * 2**20))
             self.variant_seen.append(pb.pb_matvec_get_config(ctx)["variant"])
             if args.prec == "fp64" and not self.variant64_seen:
                 self.variant64_seen.append(pb.pb_matvec_configure_fp64(ctx, 0))   # the default, as created
@@ -587,9 +595,12 @@ def run_matvec(args):
         v64 = pb.pb_matvec_configure_fp64(ctx, args.variant)
     elif args.variant:
         pb.pb_matvec_configure(ctx, args.variant, 0)
+    if args.scratch_mb:
+        pb.pb_set_scratch_limit(ctx, int(args.scratch_mb * 2**20))
     cfg = pb.pb_matvec_get_config(ctx)
     if prec == "fp64":
         cfg["variant"] = v64
+    bands, scratch = pb.pb_scratch_plan(ctx, prec)
     gen = torch.Generator(device=dev).manual_seed(7)
     u = torch.randn(2 * prob.n, dtype=torch.float64, device=dev, generator=gen)
     y = torch.empty_like(u)
@@ -629,11 +640,11 @@ def run_matvec(args):
             "dtype": {"fp64": "f64", "float2": "float-float pairs, f64 accumulation"}.get(
                 prec, "f32 pairs, f64 accumulation"), "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_triangles": prob.n,
-                       "variant": cfg["variant"], "ctas": cfg["ctas"],
+                       "variant": cfg["variant"], "ctas": cfg["ctas"], "bands": bands, "scratch_bytes": scratch,
                        "l2": "inputs L2-resident by design (the product is FP32-pipe bound)"},
             "roofline": {"kernel": kname, "bound": "alu", "achieved": value, "peak": peak, "unit": UNIT,
                          "frac": value / peak if peak else None,
-                         "traffic": MATVEC_TRAFFIC_BYTES.get((kname, args.workload)),
+                         "traffic": MATVEC_TRAFFIC_BYTES.get((kname, args.workload)) if bands <= 1 else None,
                          "peak_basis": (f"FP32 pipe: {SMS} SMs x 128 lanes x {SM_MAX_MHZ:.0f} MHz / {ops} FP32 ops "
                                         "per ordered pair (derived)") if peak else
                                        "FP64 pipe (see the ncu FP64-pipe utilisation)"},

@@ -356,6 +356,29 @@ pb_status pb_matvec_autotune(pb_ctx *ctx, int reps, int *variant, int *ctas_per_
  * variant now in use. */
 pb_status pb_matvec_configure_fp64(pb_ctx *ctx, int variant, int *variant_out);
 
+/* Bound on the device scratch of each symmetric product of this context
+ * (FP32-pair variants 5 and 6, FP64 variants 2 and 3, the float-float
+ * product), whose column sides otherwise take about 4 N^2 / B bytes (B the
+ * targets of a tile; 8 N^2 / B with FP64 column sides).  bytes = 0: no
+ * bound, one pass over all tile pairs.  pb_create sets 1 GiB, under which
+ * the FP32-pair product of up to about 365,000 triangles still runs in one
+ * pass (the FP64 and float-float ones to about 180,000).  bytes > 0: the product runs in
+ * bands of whole row tiles; after each band's pair kernel a finishing kernel
+ * completes the band's rows and adds its column sides of the later row
+ * tiles to FP64 accumulators (16 N bytes); bands hold about equal numbers of
+ * column sides, as many as the bound leaves room for after the parts that
+ * grow with N only, and at least one row tile each (so a bound below one
+ * row's column sides is exceeded).  Every row is still summed in a fixed
+ * order: results are deterministic and differ from the unbanded product only
+ * by the rounding of that order.  Frees the context's current symmetric
+ * scratch (the next product allocates it again).  bytes < 0: PB_ERR_ARG. */
+pb_status pb_set_scratch_limit(pb_ctx *ctx, int64_t bytes);
+
+/* Bands and scratch bytes of the symmetric product of precision prec at the
+ * context's current kernel choice and bound; 0 and 0 when that product is not
+ * a symmetric one.  Either pointer may be NULL.  Unknown prec: PB_ERR_ARG. */
+pb_status pb_scratch_plan(pb_ctx *ctx, pb_precision prec, int *bands, int64_t *bytes);
+
 /* Row-block product: rows [row0, row0 + nrows) of both row blocks of
  * Eqs. (12)-(13), y_rows[t] = (A u)_{row0 + t} and y_rows[nrows + t] =
  * (A u)_{N + row0 + t} for t < nrows.  u: device, 2N FP64 (all of it is

@@ -104,6 +104,8 @@ SIGNATURES = {
     "pb_matvec_get_config": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64)]),
     "pb_matvec_autotune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "pb_matvec_configure_fp64": (_I, [_VP, _I, ctypes.POINTER(_I)]),
+    "pb_set_scratch_limit": (_I, [_VP, _I64]),
+    "pb_scratch_plan": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I64)]),
     "pb_matvec_rows": (_I, [_VP, _VP, _VP, _I64, _I64, _I]),
     "pb_solve_sharded": (_I, [_VP, ctypes.POINTER(_Opts), _I, _I, _VP, _VP, _VP, _VP, ctypes.POINTER(_Info)]),
     "pb_shard_rows": (_I, [_I64, _I, _I, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
@@ -442,6 +444,20 @@ def pb_matvec_configure_fp64(ctx: Context, variant: int = 0) -> int:
     v = ctypes.c_int()
     _check(lib().pb_matvec_configure_fp64(ctx.handle, int(variant), ctypes.byref(v)), ctx)
     return v.value
+
+
+def pb_set_scratch_limit(ctx: Context, nbytes: int) -> None:
+    """Bound each symmetric product's device scratch (0: no bound); the products
+    then run in bands of row tiles."""
+    _check(lib().pb_set_scratch_limit(ctx.handle, int(nbytes)), ctx)
+
+
+def pb_scratch_plan(ctx: Context, prec="fp32pair"):
+    """(bands, scratch bytes) of the symmetric product of this precision at the
+    current kernel choice and bound; (0, 0) when that product is not symmetric."""
+    b, n = ctypes.c_int(), ctypes.c_int64()
+    _check(lib().pb_scratch_plan(ctx.handle, PRECISIONS[prec], ctypes.byref(b), ctypes.byref(n)), ctx)
+    return b.value, n.value
 
 
 def pb_matvec_autotune(ctx: Context, reps: int = 3) -> dict:

@@ -24,6 +24,8 @@
 // diagonal term.
 #include <math.h>
 
+#include <type_traits>
+
 #include "fastmath.cuh"
 #include "finish.cuh"
 #include "pb_internal.cuh"
@@ -59,20 +61,19 @@ SymPlan make_sym_plan(int64_t n, int tile, int64_t ctas_wanted) {
     return p;
 }
 
-namespace {
-int64_t round256(int64_t b) { return (b + 255) / 256 * 256; }
-}  // namespace
-
 int64_t sym64_scratch_bytes(const SymPlan &pl, int tile) {
-    return round256(pl.tiles * 2 * tile * (int64_t)sizeof(double)) +
-           round256(pl.ctas * 2 * 2 * tile * (int64_t)sizeof(double)) +
-           round256((pl.work - pl.tiles) * 2 * tile * (int64_t)sizeof(double));
+    return sym_layout(pl, tile, (int)sizeof(double), pl.work - pl.tiles, false).bytes;
 }
 
 int64_t sym_scratch_bytes(const SymPlan &pl, int tile) {
-    return round256(pl.tiles * 2 * tile * (int64_t)sizeof(double)) +
-           round256(pl.ctas * 2 * 2 * tile * (int64_t)sizeof(double)) +
-           round256((pl.work - pl.tiles) * 2 * tile * (int64_t)sizeof(float));
+    return sym_layout(pl, tile, (int)sizeof(float), pl.work - pl.tiles, false).bytes;
+}
+
+int64_t sym_scratch_need(const SymPlan &pl, int tile, int elem, int64_t limit, std::vector<int64_t> *cuts) {
+    sym_band_cuts(pl, tile, elem, limit, cuts);
+    const bool banded = cuts->size() > 2;
+    return sym_layout(pl, tile, elem, banded ? sym_max_band_slots(pl.tiles, *cuts) : pl.work - pl.tiles, banded)
+        .bytes;
 }
 
 namespace {
@@ -515,15 +516,17 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
     constexpr int STAGES = B / TS;
     static_assert(TQ == BS && B % TS == 0, "tile shapes");
     if (skip != nullptr && *((volatile const int *)skip)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
+    if (evaluated != nullptr && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
     __shared__ float4 s_a[TQ], s_b[TQ], s_c[TQ], s_d[TQ];
     __shared__ float s_col[NW][2][B];     // per-warp column sides of the current tile pair
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t c = blockIdx.x;
     const int64_t Tt = plan.tiles;
-    int64_t p = sk_begin(c, plan.work, plan.ctas);
-    const int64_t pend = sk_begin(c + 1, plan.work, plan.ctas);
+    // tile pairs [work_begin, work_begin + work) (a band of whole rows, or all of them)
+    const int64_t wb = plan.work_begin;
+    int64_t p = wb + sk_begin(c, plan.work, plan.ctas);
+    const int64_t pend = wb + sk_begin(c + 1, plan.work, plan.ctas);
     const int64_t I_first = sym_row_of(p, Tt);
     SymConsts c3;
     c3.nk2 = p_dup(prm.neg_kappa_log2e);
@@ -602,7 +605,7 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
             if (!diag) {
                 // column side of tile pair (I, J): sum over the warps in a fixed order
                 __syncthreads();
-                float *dst = jpart + sym_offdiag_index(I, J, Tt) * 2 * B;
+                float *dst = jpart + (sym_offdiag_index(I, J, Tt) - plan.joff) * 2 * B;
                 for (int x = tid; x < 2 * B; x += BS) {
                     const int r = x / B, k = x - r * B;
                     float v = s_col[0][r][k];
@@ -613,8 +616,8 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
             }
         }
         // row side of row tile I over this CTA's part of the row
-        const int64_t c0 = sk_cta_of(sym_row_start(I, Tt), plan.work, plan.ctas);
-        const int64_t c1 = sk_cta_of(row_end - 1, plan.work, plan.ctas);
+        const int64_t c0 = sk_cta_of(sym_row_start(I, Tt) - wb, plan.work, plan.ctas);
+        const int64_t c1 = sk_cta_of(row_end - 1 - wb, plan.work, plan.ctas);
         double *dst = (c0 == c1) ? iside + I * 2 * B : islots + (2 * c + (I == I_first ? 0 : 1)) * 2 * B;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
@@ -721,7 +724,7 @@ matvec_sym64_kernel(const double *__restrict__ g64, const double *__restrict__ u
                     unsigned long long *__restrict__ evaluated) {
     constexpr int BS = kF64Threads, B = BS * T, TS = BS, NW = BS / 32, STAGES = B / TS;
     if (skip != nullptr && *((volatile const int *)skip)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
+    if (evaluated != nullptr && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
     __shared__ double s_x[TS], s_y[TS], s_z[TS], s_nx[TS], s_ny[TS], s_nz[TS], s_wpsi[TS], s_wphi[TS];
     __shared__ double s_col[NW][2][B];
     const double *X = g64, *Y = g64 + N, *Z = g64 + 2 * N;
@@ -731,8 +734,9 @@ matvec_sym64_kernel(const double *__restrict__ g64, const double *__restrict__ u
     const bool hi16 = (lane & 16) != 0;
     const int64_t c = blockIdx.x;
     const int64_t Tt = plan.tiles;
-    int64_t p = sk_begin(c, plan.work, plan.ctas);
-    const int64_t pend = sk_begin(c + 1, plan.work, plan.ctas);
+    const int64_t wb = plan.work_begin;   // first tile pair of this launch's band of rows
+    int64_t p = wb + sk_begin(c, plan.work, plan.ctas);
+    const int64_t pend = wb + sk_begin(c + 1, plan.work, plan.ctas);
     const int64_t I_first = sym_row_of(p, Tt);
 
     while (p < pend) {
@@ -815,7 +819,7 @@ matvec_sym64_kernel(const double *__restrict__ g64, const double *__restrict__ u
             }
             if (!diag) {
                 __syncthreads();
-                double *dst = jpart + sym_offdiag_index(I, J, Tt) * 2 * B;
+                double *dst = jpart + (sym_offdiag_index(I, J, Tt) - plan.joff) * 2 * B;
                 for (int x = tid; x < 2 * B; x += BS) {
                     const int r = x / B, k = x - r * B;
                     double v = s_col[0][r][k];
@@ -825,8 +829,8 @@ matvec_sym64_kernel(const double *__restrict__ g64, const double *__restrict__ u
                 }
             }
         }
-        const int64_t c0 = sk_cta_of(sym_row_start(I, Tt), plan.work, plan.ctas);
-        const int64_t c1 = sk_cta_of(row_end - 1, plan.work, plan.ctas);
+        const int64_t c0 = sk_cta_of(sym_row_start(I, Tt) - wb, plan.work, plan.ctas);
+        const int64_t c1 = sk_cta_of(row_end - 1 - wb, plan.work, plan.ctas);
         double *dst = (c0 == c1) ? iside + I * 2 * B : islots + (2 * c + (I == I_first ? 0 : 1)) * 2 * B;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
@@ -948,23 +952,19 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
                 ctx->tile_counters, y, skip_flag,                                                               \
                 ctx->mv_count);                                                                                 \
     } while (0)
-#define PB_LAUNCH_SYM(T, MINB)                                                                                      \
+#define PB_LAUNCH_SYM(T, MINB)                                                                                  \
     do {                                                                                                        \
-        const SymPlan &sp = ctx->plansym;                                                                       \
-        constexpr int B = kF32Threads * T;                                                                      \
-        double *iside = (double *)ctx->sym_scratch;                                                             \
-        double *islots = iside + round256(sp.tiles * 2 * B * (int64_t)sizeof(double)) / sizeof(double);        \
-        float *jpart = (float *)(islots + round256(sp.ctas * 4 * B * (int64_t)sizeof(double)) / sizeof(double)); \
-        if (k0)                                                                                                 \
-            matvec_sym_kernel<T, true, MINB><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(               \
-                ctx->pos32, ctx->nrm32, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);    \
-        else                                                                                                    \
-            matvec_sym_kernel<T, false, MINB><<<(unsigned)sp.ctas, kF32Threads, 0, ctx->stream>>>(              \
-                ctx->pos32, ctx->nrm32, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);    \
-        matvec_sym_finalize<B, float><<<dim3((unsigned)sp.tiles, B / kSymFinRows), kSymFinThreads, 0,          \
-                                        ctx->stream>>>(                                                         \
-            u, ctx->N, diag1, diag2, sp, islots, iside, jpart, y, skip_flag);                                   \
-        PB_LAUNCHED();                                                                                          \
+        auto pair = [&](const SymPlan &bp, double *islots, double *iside, float *jpart,                         \
+                        unsigned long long *ev) {                                                               \
+            if (k0)                                                                                             \
+                matvec_sym_kernel<T, true, MINB><<<(unsigned)bp.ctas, kF32Threads, 0, ctx->stream>>>(           \
+                    ctx->pos32, ctx->nrm32, u, ctx->N, prm, bp, islots, iside, jpart, skip_flag, ev);           \
+            else                                                                                                \
+                matvec_sym_kernel<T, false, MINB><<<(unsigned)bp.ctas, kF32Threads, 0, ctx->stream>>>(          \
+                    ctx->pos32, ctx->nrm32, u, ctx->N, prm, bp, islots, iside, jpart, skip_flag, ev);           \
+        };                                                                                                      \
+        sym_enqueue<kF32Threads * T, float>(ctx->plansym, ctx->cuts32, ctx->sym_scratch, u, ctx->N, diag1,      \
+                                            diag2, y, skip_flag, ctx->mv_count, ctx->stream, pair);            \
     } while (0)
         switch (ctx->f32_variant) {
             case MV_F32_SCALAR_T4:
@@ -991,26 +991,21 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
             ctx->mv_count);
     } else {
         F64Params prm{ctx->eps, 1.0 / ctx->eps, ctx->kappa, diag1, diag2};
-        const SymPlan &sp = ctx->plansym64;
-        const int T = ctx->f64_variant == MV_F64_SYM_T2 ? 2 : 1;
-        const int B = kF64Threads * T;
-        double *iside = (double *)ctx->sym64_scratch;
-        double *islots = iside + round256(sp.tiles * 2 * B * (int64_t)sizeof(double)) / sizeof(double);
-        double *jpart = islots + round256(sp.ctas * 4 * B * (int64_t)sizeof(double)) / sizeof(double);
-        if (T == 2) {
-            matvec_sym64_kernel<2><<<(unsigned)sp.ctas, kF64Threads, 0, ctx->stream>>>(
-                ctx->g64, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);
-            matvec_sym_finalize<2 * kF64Threads, double>
-                <<<dim3((unsigned)sp.tiles, 2 * kF64Threads / kSymFinRows), kSymFinThreads, 0, ctx->stream>>>(
-                    u, ctx->N, diag1, diag2, sp, islots, iside, jpart, y, skip_flag);
-        } else {
-            matvec_sym64_kernel<1><<<(unsigned)sp.ctas, kF64Threads, 0, ctx->stream>>>(
-                ctx->g64, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);
-            matvec_sym_finalize<kF64Threads, double>
-                <<<dim3((unsigned)sp.tiles, kF64Threads / kSymFinRows), kSymFinThreads, 0, ctx->stream>>>(
-                    u, ctx->N, diag1, diag2, sp, islots, iside, jpart, y, skip_flag);
-        }
-        PB_LAUNCHED();
+        auto pair = [&](auto tag) {
+            constexpr int T = decltype(tag)::value;
+            return [&](const SymPlan &bp, double *islots, double *iside, double *jpart, unsigned long long *ev) {
+                matvec_sym64_kernel<T><<<(unsigned)bp.ctas, kF64Threads, 0, ctx->stream>>>(
+                    ctx->g64, u, ctx->N, prm, bp, islots, iside, jpart, skip_flag, ev);
+            };
+        };
+        if (ctx->f64_variant == MV_F64_SYM_T2)
+            sym_enqueue<2 * kF64Threads, double>(ctx->plansym64, ctx->cuts64, ctx->sym64_scratch, u, ctx->N, diag1,
+                                                 diag2, y, skip_flag, ctx->mv_count, ctx->stream,
+                                                 pair(std::integral_constant<int, 2>{}));
+        else
+            sym_enqueue<kF64Threads, double>(ctx->plansym64, ctx->cuts64, ctx->sym64_scratch, u, ctx->N, diag1,
+                                             diag2, y, skip_flag, ctx->mv_count, ctx->stream,
+                                             pair(std::integral_constant<int, 1>{}));
     }
     PB_LAUNCHED();
     if (timed) {
@@ -1087,12 +1082,13 @@ pb_status matvec_prepare(pb_ctx *ctx) {
     pb_status s = PB_OK;
     if (f32_variant_symmetric(ctx->f32_variant))
         s = ensure_scratch(ctx, &ctx->sym_scratch, &ctx->sym_scratch_len,
-                           sym_scratch_bytes(ctx->plansym, kF32Threads * f32_variant_targets(ctx->f32_variant)),
+                           sym_scratch_need(ctx->plansym, kF32Threads * f32_variant_targets(ctx->f32_variant),
+                                            (int)sizeof(float), ctx->scratch_limit, &ctx->cuts32),
                            "symmetric matvec scratch");
     if (s == PB_OK && ctx->f64_variant != MV_F64_PLAIN)
         s = ensure_scratch(ctx, &ctx->sym64_scratch, &ctx->sym64_scratch_len,
-                           sym64_scratch_bytes(ctx->plansym64,
-                                               kF64Threads * (ctx->f64_variant == MV_F64_SYM_T2 ? 2 : 1)),
+                           sym_scratch_need(ctx->plansym64, kF64Threads * (ctx->f64_variant == MV_F64_SYM_T2 ? 2 : 1),
+                                            (int)sizeof(double), ctx->scratch_limit, &ctx->cuts64),
                            "symmetric FP64 matvec scratch");
     return s;
 }

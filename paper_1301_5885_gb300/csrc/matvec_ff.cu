@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "fastmath.cuh"
 #include "finish.cuh"
@@ -243,7 +244,7 @@ matvec_ffsym_kernel(const double *__restrict__ g64, const double *__restrict__ u
                     unsigned long long *__restrict__ evaluated) {
     constexpr int BS = kFFThreads, B = BS * T, TS = BS, NW = BS / 32, STAGES = B / TS;
     if (skip != nullptr && *((volatile const int *)skip)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
+    if (evaluated != nullptr && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, 1ull);
     __shared__ float4 s_p[TS][4];
     __shared__ double s_col[NW][2][B];
     const double *X = g64, *Y = g64 + N, *Z = g64 + 2 * N;
@@ -252,8 +253,9 @@ matvec_ffsym_kernel(const double *__restrict__ g64, const double *__restrict__ u
     const bool hi16 = (lane & 16) != 0;
     const int64_t c = blockIdx.x;
     const int64_t Tt = plan.tiles;
-    int64_t p = sk_begin(c, plan.work, plan.ctas);
-    const int64_t pend = sk_begin(c + 1, plan.work, plan.ctas);
+    const int64_t wb = plan.work_begin;   // first tile pair of this launch's band of rows
+    int64_t p = wb + sk_begin(c, plan.work, plan.ctas);
+    const int64_t pend = wb + sk_begin(c + 1, plan.work, plan.ctas);
     const int64_t I_first = sym_row_of(p, Tt);
 
     while (p < pend) {
@@ -339,7 +341,7 @@ matvec_ffsym_kernel(const double *__restrict__ g64, const double *__restrict__ u
             }
             if (!diag) {
                 __syncthreads();
-                double *dst = jpart + sym_offdiag_index(I, J, Tt) * 2 * B;
+                double *dst = jpart + (sym_offdiag_index(I, J, Tt) - plan.joff) * 2 * B;
                 for (int x = tid; x < 2 * B; x += BS) {
                     const int r = x / B, k = x - r * B;
                     double v = s_col[0][r][k];
@@ -349,8 +351,8 @@ matvec_ffsym_kernel(const double *__restrict__ g64, const double *__restrict__ u
                 }
             }
         }
-        const int64_t c0 = sk_cta_of(sym_row_start(I, Tt), plan.work, plan.ctas);
-        const int64_t c1 = sk_cta_of(row_end - 1, plan.work, plan.ctas);
+        const int64_t c0 = sk_cta_of(sym_row_start(I, Tt) - wb, plan.work, plan.ctas);
+        const int64_t c1 = sk_cta_of(row_end - 1 - wb, plan.work, plan.ctas);
         double *dst = (c0 == c1) ? iside + I * 2 * B : islots + (2 * c + (I == I_first ? 0 : 1)) * 2 * B;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
@@ -386,6 +388,13 @@ StreamKPlan matvec_ff_plan(pb_ctx *ctx) {
 }
 
 int matvec_ff_target_tile() { return kFFTargetTile; }
+
+int64_t ff_sym_scratch_need(pb_ctx *ctx, std::vector<int64_t> *cuts) {
+    cuts->clear();
+    if (ctx->N < kFFSymMinN) return 0;
+    const int B = kFFThreads * (ctx->N >= kFFSymT2MinN ? 2 : 1);
+    return sym_scratch_need(ctx->planffsym, B, (int)sizeof(double), ctx->scratch_limit, cuts);
+}
 
 // ---------------------------------------------------------------------------
 // The source term of Eq. (11) and the energy of Eq. (14) in float-float: the
@@ -561,7 +570,7 @@ pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *
     const SymPlan &sp = ctx->planffsym;
     const int T = ctx->N >= kFFSymT2MinN ? 2 : 1;
     const int B = kFFThreads * T;
-    const int64_t need = sym64_scratch_bytes(sp, B);
+    const int64_t need = sym_scratch_need(sp, B, (int)sizeof(double), ctx->scratch_limit, &ctx->cutsff);
     if (need > ctx->symff_scratch_len) {
         // the symmetric kernel's scratch, allocated by its first product
         if (ctx->symff_scratch) ctx_free(ctx, ctx->symff_scratch);
@@ -572,24 +581,20 @@ pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *
         if (s != PB_OK) return s;
         ctx->symff_scratch_len = need;
     }
-    auto r256 = [](int64_t b) { return (b + 255) / 256 * 256; };
-    double *iside = (double *)ctx->symff_scratch;
-    double *islots = iside + r256(sp.tiles * 2 * B * (int64_t)sizeof(double)) / (int64_t)sizeof(double);
-    double *jpart = islots + r256(sp.ctas * 4 * B * (int64_t)sizeof(double)) / (int64_t)sizeof(double);
-    if (T == 2) {
-        matvec_ffsym_kernel<2><<<(unsigned)sp.ctas, kFFThreads, 0, ctx->stream>>>(
-            ctx->g64, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);
-        matvec_sym_finalize<2 * kFFThreads, double>
-            <<<dim3((unsigned)sp.tiles, 2 * kFFThreads / kSymFinRows), kSymFinThreads, 0, ctx->stream>>>(
-                u, ctx->N, prm.diag1, prm.diag2, sp, islots, iside, jpart, y, skip_flag);
-    } else {
-        matvec_ffsym_kernel<1><<<(unsigned)sp.ctas, kFFThreads, 0, ctx->stream>>>(
-            ctx->g64, u, ctx->N, prm, sp, islots, iside, jpart, skip_flag, ctx->mv_count);
-        matvec_sym_finalize<kFFThreads, double>
-            <<<dim3((unsigned)sp.tiles, kFFThreads / kSymFinRows), kSymFinThreads, 0, ctx->stream>>>(
-                u, ctx->N, prm.diag1, prm.diag2, sp, islots, iside, jpart, y, skip_flag);
-    }
-    PB_LAUNCHED();   // the finishing kernel (the caller counts the first)
+    auto pair = [&](auto tag) {
+        constexpr int TT = decltype(tag)::value;
+        return [&](const SymPlan &bp, double *islots, double *iside, double *jpart, unsigned long long *ev) {
+            matvec_ffsym_kernel<TT><<<(unsigned)bp.ctas, kFFThreads, 0, ctx->stream>>>(
+                ctx->g64, u, ctx->N, prm, bp, islots, iside, jpart, skip_flag, ev);
+        };
+    };
+    if (T == 2)
+        sym_enqueue<2 * kFFThreads, double>(sp, ctx->cutsff, ctx->symff_scratch, u, ctx->N, prm.diag1, prm.diag2, y,
+                                            skip_flag, ctx->mv_count, ctx->stream,
+                                            pair(std::integral_constant<int, 2>{}));
+    else
+        sym_enqueue<kFFThreads, double>(sp, ctx->cutsff, ctx->symff_scratch, u, ctx->N, prm.diag1, prm.diag2, y,
+                                        skip_flag, ctx->mv_count, ctx->stream, pair(std::integral_constant<int, 1>{}));
     return PB_OK;
 }
 

@@ -92,13 +92,21 @@ struct RowBlock {
 // rule as StreamKPlan.
 struct SymPlan {
     int64_t tiles;          // square tiles of the targets
-    int64_t work;           // tiles (tiles + 1) / 2 tile pairs
+    int64_t work;           // tile pairs of this launch (all tiles (tiles + 1) / 2 of them unbanded)
     int64_t ctas;
+    int64_t work_begin = 0; // first tile pair of this launch (a band of rows)
+    int64_t joff = 0;       // off-diagonal index of the band's first column side (its slot 0)
 };
 SymPlan make_sym_plan(int64_t n, int tile, int64_t ctas_wanted);
+// a new context's bound on each symmetric product's scratch: 1 GiB (the
+// FP32-pair product stays in one band up to about 365,000 triangles)
+constexpr int64_t kDefaultScratchLimit = int64_t(1) << 30;
 // device bytes of the symmetric product's scratch (row sides, split-row
 // slots, column sides per off-diagonal tile pair)
 int64_t sym_scratch_bytes(const SymPlan &pl, int tile);
+// the same under a bound of limit bytes (0: none) for column sides of elem
+// bytes; cuts receives the band cuts of row tiles (two entries: one band)
+int64_t sym_scratch_need(const SymPlan &pl, int tile, int elem, int64_t limit, std::vector<int64_t> *cuts);
 
 // ---- GMRES device state ----------------------------------------------------
 struct GmresState {
@@ -175,6 +183,10 @@ struct pb_ctx {
     pb::SymPlan plansym64{};
     void *sym64_scratch = nullptr;
     int64_t sym64_scratch_len = 0;
+    // bound on each symmetric product's scratch (bytes, 0: none) and the band
+    // cuts of row tiles each product runs in (FP32 pairs, FP64, float-float)
+    int64_t scratch_limit = pb::kDefaultScratchLimit;
+    std::vector<int64_t> cuts32, cuts64, cutsff;
     unsigned int *tile_counters = nullptr;
     int64_t counters_len = 0;
 
@@ -276,6 +288,9 @@ pb_status shard_product(pb_ctx *ctx, const double *u, double *y, pb_precision pr
 // matvec_ff.cu: the float-float product (PB_FLOAT2)
 StreamKPlan matvec_ff_plan(pb_ctx *ctx);
 int matvec_ff_target_tile();
+// scratch bytes and band cuts of the symmetric float-float product (0 and no
+// cuts below the size that uses it)
+int64_t ff_sym_scratch_need(pb_ctx *ctx, std::vector<int64_t> *cuts);
 pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *skip_flag);
 // Eq. (11) and Eq. (14) with float-float pair arithmetic (matvec_ff.cu)
 pb_status source_ff_launch(pb_ctx *ctx, double *b);

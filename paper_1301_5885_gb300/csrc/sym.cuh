@@ -5,6 +5,8 @@
 
 #include <stdint.h>
 
+#include <vector>
+
 #include "pb_internal.cuh"
 
 namespace pb {
@@ -81,6 +83,190 @@ matvec_sym_finalize(const double *__restrict__ u, int64_t N, double diag1, doubl
     }
     y[i] = diag1 * u[i] - s1;
     y[N + i] = diag2 * u[N + i] - s2;
+}
+
+// Banded form (a bound on the scratch).  The product runs as bands of whole
+// row tiles [R0, R1): the pair kernel evaluates the band's tile pairs (plan
+// with work_begin = sym_row_start(R0)) and stores only the band's column
+// sides; this kernel then finishes the band's rows and folds the band's column
+// sides of the later row tiles into FP64 accumulators colacc (tiles x 2B).
+// Block (R - R0, c), R in [R0, tiles), covers entries 64 c .. + 63 of tile R:
+// its four groups sum the band's column sides (I', R), I' = R0 + g, R0 + g + 4,
+// ... (I' < min(R, R1)), then
+//   R <  R1: y = diag u - (row side + colacc[R] + group sums in order of g),
+//            colacc[R] holding the earlier bands' column sides of R;
+//   R >= R1: colacc[R] (+)= group sums in order of g (stored by the first band).
+// Every row is summed in a fixed order, independent of the launch shape.
+template <int B, typename JT>
+__global__ void __launch_bounds__(kSymFinThreads)
+matvec_sym_band_finish(const double *__restrict__ u, int64_t N, double diag1, double diag2, SymPlan plan,
+                       int64_t R0, int64_t R1, const double *__restrict__ islots, const double *__restrict__ iside,
+                       const JT *__restrict__ jpart, double *__restrict__ colacc, double *__restrict__ y,
+                       const int *__restrict__ skip) {
+    constexpr int NG = kSymFinThreads / kSymFinRows;
+    static_assert(B % kSymFinRows == 0, "row chunks");
+    if (skip != nullptr && *((volatile const int *)skip)) return;
+    __shared__ double s_part[NG][2][kSymFinRows];
+    const int64_t Tt = plan.tiles;
+    const int64_t R = R0 + blockIdx.x;
+    const int g = threadIdx.x / kSymFinRows, kl = threadIdx.x % kSymFinRows;
+    const int k = blockIdx.y * kSymFinRows + kl;
+    const int64_t Iend = R < R1 ? R : R1;
+    double a1 = 0.0, a2 = 0.0;
+    for (int64_t Ip = R0 + g; Ip < Iend; Ip += NG) {
+        const JT *jp = jpart + (sym_offdiag_index(Ip, R, Tt) - plan.joff) * 2 * B;
+        a1 += (double)jp[k];
+        a2 += (double)jp[B + k];
+    }
+    s_part[g][0][kl] = a1;
+    s_part[g][1][kl] = a2;
+    __syncthreads();
+    if (g != 0) return;
+    double t1 = s_part[0][0][kl], t2 = s_part[0][1][kl];
+#pragma unroll
+    for (int gg = 1; gg < NG; ++gg) {
+        t1 += s_part[gg][0][kl];
+        t2 += s_part[gg][1][kl];
+    }
+    double *ca = colacc + R * 2 * B;
+    if (R >= R1) {
+        if (R0 == 0) {
+            ca[k] = t1;
+            ca[B + k] = t2;
+        } else {
+            ca[k] += t1;
+            ca[B + k] += t2;
+        }
+        return;
+    }
+    const int64_t i = R * B + k;
+    if (i >= N) return;
+    const int64_t wb = plan.work_begin;
+    const int64_t c0 = sk_cta_of(sym_row_start(R, Tt) - wb, plan.work, plan.ctas);
+    const int64_t c1 = sk_cta_of(sym_row_start(R + 1, Tt) - 1 - wb, plan.work, plan.ctas);
+    double s1 = 0.0, s2 = 0.0;
+    if (c0 == c1) {
+        s1 = iside[R * 2 * B + k];
+        s2 = iside[R * 2 * B + B + k];
+    } else {
+        for (int64_t cc = c0; cc <= c1; ++cc) {
+            const int64_t first = sym_row_of(wb + sk_begin(cc, plan.work, plan.ctas), Tt);
+            const double *sl = islots + (2 * cc + (R == first ? 0 : 1)) * 2 * B;
+            s1 += sl[k];
+            s2 += sl[B + k];
+        }
+    }
+    if (R0 > 0) {
+        s1 += ca[k];
+        s2 += ca[B + k];
+    }
+    s1 += t1;
+    s2 += t2;
+    y[i] = diag1 * u[i] - s1;
+    y[N + i] = diag2 * u[N + i] - s2;
+}
+
+// Scratch of a symmetric product with tiles of B targets and column sides of
+// elem bytes: row sides (tiles x 2B FP64), split-row slots (2 per CTA, 2B
+// FP64 each), the column sides of the largest band (2B elem each) and, when
+// banded, the FP64 column accumulators (tiles x 2B).  Offsets in bytes.
+struct SymLayout {
+    int64_t islots, jpart, colacc, bytes;
+};
+inline int64_t sym_r256(int64_t b) { return (b + 255) / 256 * 256; }
+inline SymLayout sym_layout(const SymPlan &pl, int B, int elem, int64_t slots, bool banded) {
+    SymLayout l;
+    l.islots = sym_r256(pl.tiles * 2 * B * (int64_t)sizeof(double));
+    l.jpart = l.islots + sym_r256(pl.ctas * 4 * B * (int64_t)sizeof(double));
+    l.colacc = l.jpart + sym_r256(slots * 2 * B * (int64_t)elem);
+    l.bytes = l.colacc + (banded ? sym_r256(pl.tiles * 2 * B * (int64_t)sizeof(double)) : 0);
+    return l;
+}
+
+// off-diagonal column sides of the row tiles [R0, R1)
+inline int64_t sym_band_slots(int64_t tiles, int64_t R0, int64_t R1) {
+    return (sym_row_start(R1, tiles) - R1) - (sym_row_start(R0, tiles) - R0);
+}
+
+// the plan of band [R0, R1) of a full plan: its tile pairs, CTAs and offsets
+inline SymPlan sym_band_plan(const SymPlan &full, int64_t R0, int64_t R1) {
+    SymPlan b = full;
+    b.work_begin = sym_row_start(R0, full.tiles);
+    b.work = sym_row_start(R1, full.tiles) - b.work_begin;
+    b.joff = b.work_begin - R0;
+    b.ctas = full.ctas < b.work ? full.ctas : b.work;
+    return b;
+}
+
+// Band cuts 0 = R_0 < R_1 < ... < R_m = tiles under a scratch bound of
+// limit bytes (0: one band): the bound's room for column sides split into
+// about equal bands of whole row tiles, each at most that room, or one row
+// tile where a single row's column sides exceed it.
+inline void sym_band_cuts(const SymPlan &pl, int B, int elem, int64_t limit, std::vector<int64_t> *cuts) {
+    const int64_t tiles = pl.tiles, total = sym_band_slots(tiles, 0, tiles);
+    cuts->clear();
+    cuts->push_back(0);
+    int64_t room = 0;
+    if (limit > 0) {
+        const SymLayout fixed = sym_layout(pl, B, elem, 0, true);
+        room = (limit - fixed.bytes) / (2 * B * (int64_t)elem);
+        if (room < 1) room = 1;
+    }
+    if (limit <= 0 || total <= room) {
+        cuts->push_back(tiles);
+        return;
+    }
+    const int64_t nb = (total + room - 1) / room;
+    const int64_t target = (total + nb - 1) / nb;
+    for (int64_t R0 = 0; R0 < tiles;) {
+        int64_t R1 = R0 + 1;
+        while (R1 < tiles && sym_band_slots(tiles, R0, R1 + 1) <= target) ++R1;
+        cuts->push_back(R1);
+        R0 = R1;
+    }
+}
+
+// largest band of the cuts, in column sides
+inline int64_t sym_max_band_slots(int64_t tiles, const std::vector<int64_t> &cuts) {
+    int64_t m = 0;
+    for (size_t b = 0; b + 1 < cuts.size(); ++b) {
+        const int64_t s = sym_band_slots(tiles, cuts[b], cuts[b + 1]);
+        if (s > m) m = s;
+    }
+    return m;
+}
+
+// Enqueue one symmetric product: pair(plan, islots, iside, jpart, evaluated)
+// launches the pair kernel over the plan's tile pairs, then the finishing
+// kernel runs; with more than one band, per band in order.  The product
+// counter is passed to the first band's pair kernel only.  Counts every
+// launch but one (the caller counts the product's first).
+template <int B, typename JT, typename Pair>
+void sym_enqueue(const SymPlan &sp, const std::vector<int64_t> &cuts, void *scratch, const double *u, int64_t N,
+                 double diag1, double diag2, double *y, const int *skip, unsigned long long *counter,
+                 cudaStream_t st, Pair pair) {
+    const bool banded = cuts.size() > 2;
+    const SymLayout l = sym_layout(sp, B, (int)sizeof(JT), banded ? sym_max_band_slots(sp.tiles, cuts) : 0, banded);
+    char *base = (char *)scratch;
+    double *iside = (double *)base, *islots = (double *)(base + l.islots);
+    JT *jpart = (JT *)(base + l.jpart);
+    if (!banded) {
+        pair(sp, islots, iside, jpart, counter);
+        matvec_sym_finalize<B, JT><<<dim3((unsigned)sp.tiles, B / kSymFinRows), kSymFinThreads, 0, st>>>(
+            u, N, diag1, diag2, sp, islots, iside, jpart, y, skip);
+        PB_LAUNCHED();
+        return;
+    }
+    double *colacc = (double *)(base + l.colacc);
+    for (size_t b = 0; b + 1 < cuts.size(); ++b) {
+        const int64_t R0 = cuts[b], R1 = cuts[b + 1];
+        const SymPlan bp = sym_band_plan(sp, R0, R1);
+        pair(bp, islots, iside, jpart, b == 0 ? counter : nullptr);
+        if (b > 0) PB_LAUNCHED();
+        matvec_sym_band_finish<B, JT><<<dim3((unsigned)(sp.tiles - R0), B / kSymFinRows), kSymFinThreads, 0, st>>>(
+            u, N, diag1, diag2, bp, R0, R1, islots, iside, jpart, colacc, y, skip);
+        PB_LAUNCHED();
+    }
 }
 
 }  // namespace

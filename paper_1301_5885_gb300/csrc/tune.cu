@@ -56,7 +56,9 @@ int64_t default_scratch_bytes(int64_t n, int num_sms) {
     const int v = n >= kSymT4MinN ? MV_F32_SYM_T4 : (n >= kSymT2MinN ? MV_F32_SYM_T2 : 0);
     if (v == 0) return 0;
     const int tile = kF32Threads * f32_variant_targets(v);
-    return sym_scratch_bytes(make_sym_plan(n, tile, (int64_t)num_sms * 4), tile);
+    std::vector<int64_t> cuts;
+    return sym_scratch_need(make_sym_plan(n, tile, (int64_t)num_sms * 4), tile, (int)sizeof(float),
+                            kDefaultScratchLimit, &cuts);
 }
 
 void default_f32_config(pb_ctx *ctx, int *variant, int *ctas_per_sm) {
@@ -101,6 +103,44 @@ pb_status pb_matvec_configure_fp64(pb_ctx *ctx, int variant, int *variant_out) {
     pb_status s = matvec_configure_fp64(ctx, variant);
     if (variant_out) *variant_out = ctx->f64_variant;
     return s;
+}
+
+pb_status pb_set_scratch_limit(pb_ctx *ctx, int64_t bytes) {
+    if (!ctx) return set_error(nullptr, PB_ERR_ARG, "pb_set_scratch_limit: NULL context");
+    if (bytes < 0) return set_error(ctx, PB_ERR_ARG, "pb_set_scratch_limit: negative bound %lld", (long long)bytes);
+    // the next product of each kind allocates its scratch again (freed in stream order)
+    void **bufs[3] = {&ctx->sym_scratch, &ctx->sym64_scratch, &ctx->symff_scratch};
+    int64_t *lens[3] = {&ctx->sym_scratch_len, &ctx->sym64_scratch_len, &ctx->symff_scratch_len};
+    for (int k = 0; k < 3; ++k) {
+        if (*bufs[k]) ctx_free(ctx, *bufs[k]);
+        ctx->device_bytes -= *lens[k];
+        *bufs[k] = nullptr;
+        *lens[k] = 0;
+    }
+    ctx->scratch_limit = bytes;
+    return PB_OK;
+}
+
+pb_status pb_scratch_plan(pb_ctx *ctx, pb_precision prec, int *bands, int64_t *bytes) {
+    if (!ctx) return set_error(nullptr, PB_ERR_ARG, "pb_scratch_plan: NULL context");
+    std::vector<int64_t> cuts;
+    int64_t need = 0;
+    if (prec == PB_FP32PAIR) {
+        if (f32_variant_symmetric(ctx->f32_variant))
+            need = sym_scratch_need(ctx->plansym, kF32Threads * f32_variant_targets(ctx->f32_variant),
+                                    (int)sizeof(float), ctx->scratch_limit, &cuts);
+    } else if (prec == PB_FP64) {
+        if (ctx->f64_variant != MV_F64_PLAIN)
+            need = sym_scratch_need(ctx->plansym64, kF64Threads * (ctx->f64_variant == MV_F64_SYM_T2 ? 2 : 1),
+                                    (int)sizeof(double), ctx->scratch_limit, &cuts);
+    } else if (prec == PB_FLOAT2) {
+        need = ff_sym_scratch_need(ctx, &cuts);
+    } else {
+        return set_error(ctx, PB_ERR_ARG, "pb_scratch_plan: unknown precision %d", (int)prec);
+    }
+    if (bands) *bands = cuts.empty() ? 0 : (int)cuts.size() - 1;
+    if (bytes) *bytes = need;
+    return PB_OK;
 }
 
 pb_status pb_matvec_autotune(pb_ctx *ctx, int reps, int *variant, int *ctas_per_sm, double *best_ms) {
