@@ -212,9 +212,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// r^2 is clamped from below before the MUFU rsqrt / rcp, so 1/rho <= 1e9 and
-// 1/rho^2 <= 1e18; rho = r^2 (1/rho) takes the unclamped r^2 and is exactly 0
-// for a pair at zero distance.
+// r^2 is clamped from below before the MUFU rsqrt / rcp (the symmetric kernel
+// adds it, one packed add instead of two max, the same for any r^2 of a
+// mesh), so 1/rho <= 1e9 and 1/rho^2 <= 1e18; rho = r^2 (1/rho) takes the
+// unclamped r^2 and is exactly 0 for a pair at zero distance.
 constexpr float kRho2Min = 1e-18f;
 
 template <int T, bool K0>
@@ -371,7 +372,7 @@ matvec_f32x2_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ n
 // the constants (eps - 1) and (1 - 1/eps) folded into the weights.
 // ---------------------------------------------------------------------------
 struct SymConsts {
-    float2 nk2, mkap2, one2, mone2, mthree2, three2, meps2, epsm1, ieps2, omieps;
+    float2 nk2, mkap2, one2, mone2, mthree2, three2, meps2, epsm1, ieps2, omieps, rho2min;
 };
 
 // The warp reduce-scatter of four values (lanes 0-7 end with the total of the
@@ -391,8 +392,7 @@ struct WarpReduce4 {
     }
     __device__ __forceinline__ void step(int st, bool hi8) {
         if (st == 1) {
-            keep.x += recv.x;
-            keep.y += recv.y;
+            keep = p_add(keep, recv);
             k = hi8 ? keep.y : keep.x;
             o = __shfl_xor_sync(0xffffffffu, hi8 ? keep.x : keep.y, 8);
         } else {
@@ -435,14 +435,15 @@ __device__ __forceinline__ void sym_stage(const float4 *s_a, const float4 *s_b, 
             const float2 dx = p_add(xi[t], mx), dy = p_add(yi[t], my), dz = p_add(zi[t], mz);
             const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
             float2 inv, inv2;
-            const float r2cx = fmaxf(r2.x, kRho2Min), r2cy = fmaxf(r2.y, kRho2Min);
-            inv.x = rsqrt_approx(r2cx);
-            inv.y = rsqrt_approx(r2cy);
+            // r^2 + 1e-18: the same as the floor for any r^2 above 2e-11 and for r^2 = 0
+            const float2 r2c = p_add(r2, k.rho2min);
+            inv.x = rsqrt_approx(r2c.x);
+            inv.y = rsqrt_approx(r2c.y);
             if (K0) {
                 inv2 = p_mul(inv, inv);
             } else {
-                inv2.x = rcp_approx(r2cx);
-                inv2.y = rcp_approx(r2cy);
+                inv2.x = rcp_approx(r2c.x);
+                inv2.y = rcp_approx(r2c.y);
             }
             const float2 inv3 = p_mul(inv2, inv);
             const float2 ncx = p_fma(dx, nxi[t], p_fma(dy, nyi[t], p_mul(dz, nzi[t])));   // -c_x
@@ -539,6 +540,7 @@ matvec_sym_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm
     c3.epsm1 = p_dup(prm.eps - 1.f);
     c3.ieps2 = p_dup(prm.inv_eps);
     c3.omieps = p_dup(1.f - prm.inv_eps);
+    c3.rho2min = p_dup(kRho2Min);
     // kappa = 0: a = (eps - 1)/rho^3 and -b = (1 - 1/eps)/rho^3, constants folded into the weights
     const float wphi_scale = K0 ? prm.eps - 1.f : 1.f, wpsi_scale = K0 ? 1.f - prm.inv_eps : 1.f;
 
