@@ -423,8 +423,8 @@ __device__ __forceinline__ void sym_stage(const float4 *s_a, const float4 *s_b, 
     const int cbase = (lane >> 4) * B + ((lane >> 3) & 1);
     const bool writer = (lane & 7) == 0;
     WarpReduce4 red;
-    // source pairs unrolled 8-fold (measured best: 1204 -> 1298 Gpairs/s from 1 to 8, 16
-    // spills), 16-fold for the shorter kappa = 0 body (+0.9 % over 8, no spills)
+    // source pairs unrolled 8-fold (measured: 1204 -> 1298 Gpairs/s from 1 to 8, 1004 at
+    // 16), 16-fold for the shorter kappa = 0 body (+0.9 % over 8)
     constexpr int kUnr = K0 ? 16 : 8;
 #pragma unroll kUnr
     for (int q = 0; q < npairs; ++q) {
