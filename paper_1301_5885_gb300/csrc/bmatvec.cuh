@@ -297,8 +297,16 @@ __device__ __forceinline__ void bstage(const float4 *s_g, const float4 *s_w, int
 // by the last to arrive, which adds the partial rows in CTA order.
 // T targets per thread (target tile 128 T); ACCM places the row sums of the
 // thread's 2 R T rows (see BmvRowSums).
+// Resident CTAs per SM the register allocation must allow (0: the compiler's
+// choice).  Two targets per thread with 8 right-hand sides and float-float row
+// sums in shared memory is held to 170 registers, three CTAs per SM; left to
+// itself the allocation takes 186 and two.
+constexpr int bmv_min_blocks(int R, int T, int ACCM) {
+    return (R == 8 && T == 2 && ACCM == BMV_FF_SHARED) ? 3 : 0;
+}
+
 template <int R, int T, int ACCM>
-__global__ void __launch_bounds__(kBThreads)
+__global__ void __launch_bounds__(kBThreads, bmv_min_blocks(R, T, ACCM))
 bmatvec_kernel(const BSurf *__restrict__ surf, int nsurf, const BInst *__restrict__ inst,
                const int64_t *__restrict__ wbase, int64_t G,
                int usel, int k, const int *__restrict__ active, double *__restrict__ partials,
