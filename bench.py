@@ -61,8 +61,8 @@ MATVEC_KERNELS = {
     2: ("matvec_f32x2_kernel<2>", 39, 18),
     3: ("matvec_f32x2_kernel<4>", 39, 18),
     4: ("matvec_f32x2_kernel<3>", 39, 18),
-    5: ("matvec_sym_kernel<2> + matvec_sym_finalize<2>", 23, 10),
-    6: ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", 23, 10),
+    5: ("matvec_sym_kernel<2> + finishing kernels", 23, 10),
+    6: ("matvec_sym_kernel<4> + finishing kernels", 23, 10),
 }
 
 
@@ -77,14 +77,12 @@ def matvec_peak_gpairs(ops_per_pair):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel on
 # the 81,920-triangle sphere, from an ncu capture of the kernel as it is now
 # (profiles/); a kernel that changed since its capture has no entry.
+# DRAM bytes of one product by (kernel, workload, bands), from ncu captures
+# without the cache flush (as in a solve); a configuration not captured
+# reports no traffic
 MATVEC_TRAFFIC_BYTES = {
-    # profiles/matvec_sym_kernel_sphere2_full.md: both kernels of one product,
-    # ncu cold-cache replay (the finishing kernel's 58 MB come from L2 in a solve)
-    ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", "sphere2"): 4009728 + 2661120 + 58419712 + 25088,
-    # profiles/matvec_sym_kernel_protein300k_traffic.md: both kernels of one
-    # product on the 300,176-triangle solute, ncu without its cache flush (as in
-    # a solve; the column sides exceed L2 and go through DRAM), MB to 0.1
-    ("matvec_sym_kernel<4> + matvec_sym_finalize<4>", "protein300k"): (30.4 + 660.7 + 716.9 + 64.9) * 1e6,
+    # profiles/matvec_sym_kernel_protein300k_traffic.md: one pass, MB to 0.1
+    ("matvec_sym_kernel<4> + finishing kernels", "protein300k", 1): (30.4 + 660.7 + 716.9 + 64.9) * 1e6,
 }
 
 WORKLOADS = {
@@ -134,7 +132,10 @@ def parse():
                     help="matvec mode: FP32-pair kernel variant (0: the library's default for N)")
     ap.add_argument("--scratch-mb", type=float, default=0.0,
                     help="solve/matvec modes: bound on the symmetric product's scratch in MiB "
-                         "(0: none; bounded, the product runs in bands of row tiles)")
+                         "(0: the library's default bound, 1 GiB)")
+    ap.add_argument("--bands", type=int, default=-1,
+                    help="solve/matvec modes: bands of the symmetric product (-1: the library's default, "
+                         "automatic; 1: one pass; n >= 2: at least n)")
     ap.add_argument("--n-solutes", type=int, default=64, help="batch mode: solutes per batch")
     ap.add_argument("--frames", type=int, default=20, help="frames mode: trajectory length")
     ap.add_argument("--batch-shape", default=None,
@@ -284,6 +285,8 @@ def config_dict(args, prob):
          "l2": "flushed between steps (256 MiB write)"}
     if getattr(args, "scratch_mb", 0):
         d["scratch_bound_mib"] = args.scratch_mb
+    if getattr(args, "bands", -1) >= 0:
+        d["bands_requested"] = args.bands
     return d
 
 
@@ -310,6 +313,7 @@ class SolveLeg:
     def __init__(self, pb, prob, args, tol, stream):
         self.pb, self.prob, self.args, self.tol, self.stream = pb, prob, args, tol, stream
         self.variant_seen, self.variant64_seen = [], []
+        self.bands_seen = (0, 0)
 
     def step(self, c, nr, a, q, profile=False):
         pb, prob, args = self.pb, self.prob, self.args
@@ -317,7 +321,10 @@ class SolveLeg:
         try:
             if args.scratch_mb:
                 pb.pb_set_scratch_limit(ctx, int(args.scratch_mb * 2**20))
+            if args.bands >= 0:
+                pb.pb_set_bands(ctx, args.bands)
             self.variant_seen.append(pb.pb_matvec_get_config(ctx)["variant"])
+            self.bands_seen = pb.pb_scratch_plan(ctx, args.prec)
             if args.prec == "fp64" and not self.variant64_seen:
                 self.variant64_seen.append(pb.pb_matvec_configure_fp64(ctx, 0))   # the default, as created
             if profile:
@@ -362,7 +369,8 @@ class SolveLeg:
         peak = matvec_peak_gpairs(ops) if ops else None
         out = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
                "frac": achieved / peak if peak else None,
-               "traffic": MATVEC_TRAFFIC_BYTES.get((kname, self.args.workload)),
+               "traffic": MATVEC_TRAFFIC_BYTES.get((kname, self.args.workload, self.bands_seen[0])),
+               "bands": self.bands_seen[0], "scratch_bytes": self.bands_seen[1],
                "peak_basis": (f"FP32 pipe: {SMS} SMs x 128 lanes x {SM_MAX_MHZ:.0f} MHz / {ops} FP32 ops per "
                               "ordered pair, the kernel's own count (derived from unit counts and the maximum "
                               "SM clock; not a measured peak)") if ops else "FP64 pipe",
@@ -598,6 +606,8 @@ def run_matvec(args):
         pb.pb_matvec_configure(ctx, args.variant, 0)
     if args.scratch_mb:
         pb.pb_set_scratch_limit(ctx, int(args.scratch_mb * 2**20))
+    if args.bands >= 0:
+        pb.pb_set_bands(ctx, args.bands)
     cfg = pb.pb_matvec_get_config(ctx)
     if prec == "fp64":
         cfg["variant"] = v64
@@ -645,7 +655,7 @@ def run_matvec(args):
                        "l2": "inputs L2-resident by design (the product is FP32-pipe bound)"},
             "roofline": {"kernel": kname, "bound": "alu", "achieved": value, "peak": peak, "unit": UNIT,
                          "frac": value / peak if peak else None,
-                         "traffic": MATVEC_TRAFFIC_BYTES.get((kname, args.workload)) if bands <= 1 else None,
+                         "traffic": MATVEC_TRAFFIC_BYTES.get((kname, args.workload, max(bands, 1))),
                          "peak_basis": (f"FP32 pipe: {SMS} SMs x 128 lanes x {SM_MAX_MHZ:.0f} MHz / {ops} FP32 ops "
                                         "per ordered pair (derived)") if peak else
                                        "FP64 pipe (see the ncu FP64-pipe utilisation)"},

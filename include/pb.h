@@ -356,27 +356,44 @@ pb_status pb_matvec_autotune(pb_ctx *ctx, int reps, int *variant, int *ctas_per_
  * variant now in use. */
 pb_status pb_matvec_configure_fp64(pb_ctx *ctx, int variant, int *variant_out);
 
-/* Bound on the device scratch of each symmetric product of this context
- * (FP32-pair variants 5 and 6, FP64 variants 2 and 3, the float-float
- * product), whose column sides otherwise take about 4 N^2 / B bytes (B the
- * targets of a tile; 8 N^2 / B with FP64 column sides).  bytes = 0: no
- * bound, one pass over all tile pairs.  pb_create sets 1 GiB, under which
- * the FP32-pair product of up to about 365,000 triangles still runs in one
- * pass (the FP64 and float-float ones to about 180,000).  bytes > 0: the product runs in
- * bands of whole row tiles; after each band's pair kernel a finishing kernel
- * completes the band's rows and adds its column sides of the later row
- * tiles to FP64 accumulators (16 N bytes); bands hold about equal numbers of
- * column sides, as many as the bound leaves room for after the parts that
- * grow with N only, and at least one row tile each (so a bound below one
- * row's column sides is exceeded).  Every row is still summed in a fixed
- * order: results are deterministic and differ from the unbanded product only
- * by the rounding of that order.  Frees the context's current symmetric
- * scratch (the next product allocates it again).  bytes < 0: PB_ERR_ARG. */
+/* Bands of the symmetric products (FP32-pair variants 5 and 6, FP64
+ * variants 2 and 3, the float-float product).  Their column sides take about
+ * 4 N^2 / B bytes of device scratch in one pass (B the targets of a tile;
+ * 8 N^2 / B with FP64 column sides).  In bands, the product runs over whole
+ * row tiles at a time, with about equal numbers of column sides per band:
+ * each band's pair kernel is followed by a finishing kernel that completes
+ * the band's rows and adds its column sides of the later row tiles to FP64
+ * accumulators (16 N bytes), and consecutive bands alternate between the
+ * context's stream and a second one (created by the first banded product),
+ * so that a band's pair kernel fills the SMs that the previous one's last
+ * CTAs leave idle; two sets of slots and column sides are kept for that.
+ * Every row is still summed in a fixed order: results are deterministic and
+ * differ from the one-pass product only by the rounding of that order.
+ *
+ * pb_set_scratch_limit: bound on each symmetric product's scratch in bytes;
+ * 0: none.  pb_create sets 1 GiB, under which the FP32-pair product of up to
+ * about 365,000 triangles needs no band for memory (the FP64 and float-float
+ * ones to about 180,000).  Bands take as many column sides as the bound leaves
+ * room for after the parts that grow with N only, and at least one row tile
+ * each (so a bound below one row's column sides is exceeded).  Frees the
+ * context's current symmetric scratch (the next product allocates it again).
+ * bytes < 0: PB_ERR_ARG.
+ *
+ * pb_set_bands: bands requested besides the bound.  0 (the default):
+ * automatic, as many as give every CTA of the product's persistent grid at
+ * least 5 tile pairs per band, at most 24 (for the FP32-pair product: one
+ * pass below about 28,000 triangles, 6 bands at 81,920, about 24 at 300,000);
+ * 1: none; n >= 2: at least n (or one row tile per band where the row
+ * tiles are fewer).  Except for n >= 2, a product takes one pass
+ * whenever bands would need more scratch than one pass.  Takes effect at the
+ * next product.  bands < 0: PB_ERR_ARG. */
 pb_status pb_set_scratch_limit(pb_ctx *ctx, int64_t bytes);
+pb_status pb_set_bands(pb_ctx *ctx, int bands);
 
 /* Bands and scratch bytes of the symmetric product of precision prec at the
- * context's current kernel choice and bound; 0 and 0 when that product is not
- * a symmetric one.  Either pointer may be NULL.  Unknown prec: PB_ERR_ARG. */
+ * context's current kernel choice, bound and band request; 0 and 0 when that
+ * product is not a symmetric one.  Either pointer may be NULL.  Unknown prec:
+ * PB_ERR_ARG. */
 pb_status pb_scratch_plan(pb_ctx *ctx, pb_precision prec, int *bands, int64_t *bytes);
 
 /* Row-block product: rows [row0, row0 + nrows) of both row blocks of

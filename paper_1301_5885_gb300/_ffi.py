@@ -105,6 +105,7 @@ SIGNATURES = {
     "pb_matvec_autotune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "pb_matvec_configure_fp64": (_I, [_VP, _I, ctypes.POINTER(_I)]),
     "pb_set_scratch_limit": (_I, [_VP, _I64]),
+    "pb_set_bands": (_I, [_VP, _I]),
     "pb_scratch_plan": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I64)]),
     "pb_matvec_rows": (_I, [_VP, _VP, _VP, _I64, _I64, _I]),
     "pb_solve_sharded": (_I, [_VP, ctypes.POINTER(_Opts), _I, _I, _VP, _VP, _VP, _VP, ctypes.POINTER(_Info)]),
@@ -450,6 +451,12 @@ def pb_set_scratch_limit(ctx: Context, nbytes: int) -> None:
     """Bound each symmetric product's device scratch (0: no bound); the products
     then run in bands of row tiles."""
     _check(lib().pb_set_scratch_limit(ctx.handle, int(nbytes)), ctx)
+
+
+def pb_set_bands(ctx: Context, bands: int) -> None:
+    """Bands of the symmetric products: 0 automatic (the default), 1 none,
+    n >= 2 at least n."""
+    _check(lib().pb_set_bands(ctx.handle, int(bands)), ctx)
 
 
 def pb_scratch_plan(ctx: Context, prec="fp32pair"):

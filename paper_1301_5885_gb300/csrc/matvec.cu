@@ -69,8 +69,9 @@ int64_t sym_scratch_bytes(const SymPlan &pl, int tile) {
     return sym_layout(pl, tile, (int)sizeof(float), pl.work - pl.tiles, false).bytes;
 }
 
-int64_t sym_scratch_need(const SymPlan &pl, int tile, int elem, int64_t limit, std::vector<int64_t> *cuts) {
-    sym_band_cuts(pl, tile, elem, limit, cuts);
+int64_t sym_scratch_need(const SymPlan &pl, int tile, int elem, int64_t limit, int bands,
+                         std::vector<int64_t> *cuts) {
+    sym_band_cuts(pl, tile, elem, limit, bands, cuts);
     const bool banded = cuts->size() > 2;
     return sym_layout(pl, tile, elem, banded ? sym_max_band_slots(pl.tiles, *cuts) : pl.work - pl.tiles, banded)
         .bytes;
@@ -934,6 +935,7 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         }
         cudaEventRecord(ctx->prof_ev[ctx->prof_used], ctx->stream);
     }
+    cudaError_t sym_e = cudaSuccess;
     if (prec == PB_FP32PAIR) {
         F32Params prm;
         prm.eps = (float)ctx->eps;
@@ -960,16 +962,17 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
 #define PB_LAUNCH_SYM(T, MINB)                                                                                  \
     do {                                                                                                        \
         auto pair = [&](const SymPlan &bp, double *islots, double *iside, float *jpart,                         \
-                        unsigned long long *ev) {                                                               \
+                        unsigned long long *ev, cudaStream_t s) {                                               \
             if (k0)                                                                                             \
-                matvec_sym_kernel<T, true, MINB><<<(unsigned)bp.ctas, kF32Threads, 0, ctx->stream>>>(           \
+                matvec_sym_kernel<T, true, MINB><<<(unsigned)bp.ctas, kF32Threads, 0, s>>>(                     \
                     ctx->pos32, ctx->nrm32, u, ctx->N, prm, bp, islots, iside, jpart, skip_flag, ev);           \
             else                                                                                                \
-                matvec_sym_kernel<T, false, MINB><<<(unsigned)bp.ctas, kF32Threads, 0, ctx->stream>>>(          \
+                matvec_sym_kernel<T, false, MINB><<<(unsigned)bp.ctas, kF32Threads, 0, s>>>(                    \
                     ctx->pos32, ctx->nrm32, u, ctx->N, prm, bp, islots, iside, jpart, skip_flag, ev);           \
         };                                                                                                      \
-        sym_enqueue<kF32Threads * T, float>(ctx->plansym, ctx->cuts32, ctx->sym_scratch, u, ctx->N, diag1,      \
-                                            diag2, y, skip_flag, ctx->mv_count, ctx->stream, pair);            \
+        sym_e = sym_enqueue<kF32Threads * T, float>(ctx->plansym, ctx->cuts32, ctx->sym_scratch, u, ctx->N,     \
+                                                    diag1, diag2, y, skip_flag, ctx->mv_count, ctx->stream,    \
+                                                    ctx->band_stream, ctx->band_ev, pair);                     \
     } while (0)
         switch (ctx->f32_variant) {
             case MV_F32_SCALAR_T4:
@@ -998,20 +1001,24 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         F64Params prm{ctx->eps, 1.0 / ctx->eps, ctx->kappa, diag1, diag2};
         auto pair = [&](auto tag) {
             constexpr int T = decltype(tag)::value;
-            return [&](const SymPlan &bp, double *islots, double *iside, double *jpart, unsigned long long *ev) {
-                matvec_sym64_kernel<T><<<(unsigned)bp.ctas, kF64Threads, 0, ctx->stream>>>(
+            return [&](const SymPlan &bp, double *islots, double *iside, double *jpart, unsigned long long *ev,
+                       cudaStream_t s) {
+                matvec_sym64_kernel<T><<<(unsigned)bp.ctas, kF64Threads, 0, s>>>(
                     ctx->g64, u, ctx->N, prm, bp, islots, iside, jpart, skip_flag, ev);
             };
         };
         if (ctx->f64_variant == MV_F64_SYM_T2)
-            sym_enqueue<2 * kF64Threads, double>(ctx->plansym64, ctx->cuts64, ctx->sym64_scratch, u, ctx->N, diag1,
-                                                 diag2, y, skip_flag, ctx->mv_count, ctx->stream,
-                                                 pair(std::integral_constant<int, 2>{}));
+            sym_e = sym_enqueue<2 * kF64Threads, double>(ctx->plansym64, ctx->cuts64, ctx->sym64_scratch, u, ctx->N,
+                                                         diag1, diag2, y, skip_flag, ctx->mv_count, ctx->stream,
+                                                         ctx->band_stream, ctx->band_ev,
+                                                         pair(std::integral_constant<int, 2>{}));
         else
-            sym_enqueue<kF64Threads, double>(ctx->plansym64, ctx->cuts64, ctx->sym64_scratch, u, ctx->N, diag1,
-                                             diag2, y, skip_flag, ctx->mv_count, ctx->stream,
-                                             pair(std::integral_constant<int, 1>{}));
+            sym_e = sym_enqueue<kF64Threads, double>(ctx->plansym64, ctx->cuts64, ctx->sym64_scratch, u, ctx->N,
+                                                     diag1, diag2, y, skip_flag, ctx->mv_count, ctx->stream,
+                                                     ctx->band_stream, ctx->band_ev,
+                                                     pair(std::integral_constant<int, 1>{}));
     }
+    if (sym_e != cudaSuccess) return cuda_error(ctx, sym_e, "symmetric product bands");
     PB_LAUNCHED();
     if (timed) {
         cudaEventRecord(ctx->prof_ev[ctx->prof_used + 1], ctx->stream);
@@ -1083,18 +1090,30 @@ pb_status ensure_scratch(pb_ctx *ctx, void **buf, int64_t *len, int64_t need, co
 }
 }  // namespace
 
+pb_status ensure_band_streams(pb_ctx *ctx) {
+    if (ctx->band_stream) return PB_OK;
+    // the second stream of a banded product, at the priority of the context's stream
+    int prio = 0;
+    cudaError_t e = ctx->stream ? cudaStreamGetPriority(ctx->stream, &prio) : cudaSuccess;
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->band_stream, cudaStreamNonBlocking, prio);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        e = cudaEventCreateWithFlags(&ctx->band_ev[k], cudaEventDisableTiming);
+    return e == cudaSuccess ? PB_OK : cuda_error(ctx, e, "band streams");
+}
+
 pb_status matvec_prepare(pb_ctx *ctx) {
     pb_status s = PB_OK;
     if (f32_variant_symmetric(ctx->f32_variant))
         s = ensure_scratch(ctx, &ctx->sym_scratch, &ctx->sym_scratch_len,
                            sym_scratch_need(ctx->plansym, kF32Threads * f32_variant_targets(ctx->f32_variant),
-                                            (int)sizeof(float), ctx->scratch_limit, &ctx->cuts32),
+                                            (int)sizeof(float), ctx->scratch_limit, ctx->bands, &ctx->cuts32),
                            "symmetric matvec scratch");
     if (s == PB_OK && ctx->f64_variant != MV_F64_PLAIN)
         s = ensure_scratch(ctx, &ctx->sym64_scratch, &ctx->sym64_scratch_len,
                            sym_scratch_need(ctx->plansym64, kF64Threads * (ctx->f64_variant == MV_F64_SYM_T2 ? 2 : 1),
-                                            (int)sizeof(double), ctx->scratch_limit, &ctx->cuts64),
+                                            (int)sizeof(double), ctx->scratch_limit, ctx->bands, &ctx->cuts64),
                            "symmetric FP64 matvec scratch");
+    if (s == PB_OK && (ctx->cuts32.size() > 2 || ctx->cuts64.size() > 2)) s = ensure_band_streams(ctx);
     return s;
 }
 

@@ -393,7 +393,7 @@ int64_t ff_sym_scratch_need(pb_ctx *ctx, std::vector<int64_t> *cuts) {
     cuts->clear();
     if (ctx->N < kFFSymMinN) return 0;
     const int B = kFFThreads * (ctx->N >= kFFSymT2MinN ? 2 : 1);
-    return sym_scratch_need(ctx->planffsym, B, (int)sizeof(double), ctx->scratch_limit, cuts);
+    return sym_scratch_need(ctx->planffsym, B, (int)sizeof(double), ctx->scratch_limit, ctx->bands, cuts);
 }
 
 // ---------------------------------------------------------------------------
@@ -570,7 +570,7 @@ pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *
     const SymPlan &sp = ctx->planffsym;
     const int T = ctx->N >= kFFSymT2MinN ? 2 : 1;
     const int B = kFFThreads * T;
-    const int64_t need = sym_scratch_need(sp, B, (int)sizeof(double), ctx->scratch_limit, &ctx->cutsff);
+    const int64_t need = sym_scratch_need(sp, B, (int)sizeof(double), ctx->scratch_limit, ctx->bands, &ctx->cutsff);
     if (need > ctx->symff_scratch_len) {
         // the symmetric kernel's scratch, allocated by its first product
         if (ctx->symff_scratch) ctx_free(ctx, ctx->symff_scratch);
@@ -581,21 +581,28 @@ pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *
         if (s != PB_OK) return s;
         ctx->symff_scratch_len = need;
     }
+    if (ctx->cutsff.size() > 2) {
+        pb_status bs = ensure_band_streams(ctx);
+        if (bs != PB_OK) return bs;
+    }
     auto pair = [&](auto tag) {
         constexpr int TT = decltype(tag)::value;
-        return [&](const SymPlan &bp, double *islots, double *iside, double *jpart, unsigned long long *ev) {
-            matvec_ffsym_kernel<TT><<<(unsigned)bp.ctas, kFFThreads, 0, ctx->stream>>>(
+        return [&](const SymPlan &bp, double *islots, double *iside, double *jpart, unsigned long long *ev,
+                   cudaStream_t s) {
+            matvec_ffsym_kernel<TT><<<(unsigned)bp.ctas, kFFThreads, 0, s>>>(
                 ctx->g64, u, ctx->N, prm, bp, islots, iside, jpart, skip_flag, ev);
         };
     };
+    cudaError_t e;
     if (T == 2)
-        sym_enqueue<2 * kFFThreads, double>(sp, ctx->cutsff, ctx->symff_scratch, u, ctx->N, prm.diag1, prm.diag2, y,
-                                            skip_flag, ctx->mv_count, ctx->stream,
-                                            pair(std::integral_constant<int, 2>{}));
+        e = sym_enqueue<2 * kFFThreads, double>(sp, ctx->cutsff, ctx->symff_scratch, u, ctx->N, prm.diag1, prm.diag2,
+                                                y, skip_flag, ctx->mv_count, ctx->stream, ctx->band_stream,
+                                                ctx->band_ev, pair(std::integral_constant<int, 2>{}));
     else
-        sym_enqueue<kFFThreads, double>(sp, ctx->cutsff, ctx->symff_scratch, u, ctx->N, prm.diag1, prm.diag2, y,
-                                        skip_flag, ctx->mv_count, ctx->stream, pair(std::integral_constant<int, 1>{}));
-    return PB_OK;
+        e = sym_enqueue<kFFThreads, double>(sp, ctx->cutsff, ctx->symff_scratch, u, ctx->N, prm.diag1, prm.diag2, y,
+                                            skip_flag, ctx->mv_count, ctx->stream, ctx->band_stream, ctx->band_ev,
+                                            pair(std::integral_constant<int, 1>{}));
+    return e == cudaSuccess ? PB_OK : cuda_error(ctx, e, "symmetric float-float product bands");
 }
 
 pb_status source_ff_launch(pb_ctx *ctx, double *b) {

@@ -160,6 +160,12 @@ void free_all(pb_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
     ctx->prof_ev.clear();
+    for (cudaEvent_t &ev : ctx->band_ev) {
+        if (ev) cudaEventDestroy(ev);
+        ev = nullptr;
+    }
+    if (ctx->band_stream) cudaStreamDestroy(ctx->band_stream);
+    ctx->band_stream = nullptr;
     pinned_free(ctx->host_scalar, 16 * sizeof(double));
     pinned_free(ctx->st_host, sizeof(GmresState));
 }

@@ -106,7 +106,8 @@ constexpr int64_t kDefaultScratchLimit = int64_t(1) << 30;
 int64_t sym_scratch_bytes(const SymPlan &pl, int tile);
 // the same under a bound of limit bytes (0: none) for column sides of elem
 // bytes; cuts receives the band cuts of row tiles (two entries: one band)
-int64_t sym_scratch_need(const SymPlan &pl, int tile, int elem, int64_t limit, std::vector<int64_t> *cuts);
+int64_t sym_scratch_need(const SymPlan &pl, int tile, int elem, int64_t limit, int bands,
+                         std::vector<int64_t> *cuts);
 
 // ---- GMRES device state ----------------------------------------------------
 struct GmresState {
@@ -186,7 +187,11 @@ struct pb_ctx {
     // bound on each symmetric product's scratch (bytes, 0: none) and the band
     // cuts of row tiles each product runs in (FP32 pairs, FP64, float-float)
     int64_t scratch_limit = pb::kDefaultScratchLimit;
+    int bands = 0;                 // requested bands: 0 automatic, 1 none, n >= 2 at least n
     std::vector<int64_t> cuts32, cuts64, cutsff;
+    // second stream and events of a banded product (created by its first one)
+    cudaStream_t band_stream = nullptr;
+    cudaEvent_t band_ev[3] = {nullptr, nullptr, nullptr};
     unsigned int *tile_counters = nullptr;
     int64_t counters_len = 0;
 
@@ -288,6 +293,8 @@ pb_status shard_product(pb_ctx *ctx, const double *u, double *y, pb_precision pr
 // matvec_ff.cu: the float-float product (PB_FLOAT2)
 StreamKPlan matvec_ff_plan(pb_ctx *ctx);
 int matvec_ff_target_tile();
+// the second stream and events of banded symmetric products (matvec.cu)
+pb_status ensure_band_streams(pb_ctx *ctx);
 // scratch bytes and band cuts of the symmetric float-float product (0 and no
 // cuts below the size that uses it)
 int64_t ff_sym_scratch_need(pb_ctx *ctx, std::vector<int64_t> *cuts);

@@ -168,17 +168,23 @@ matvec_sym_band_finish(const double *__restrict__ u, int64_t N, double diag1, do
 
 // Scratch of a symmetric product with tiles of B targets and column sides of
 // elem bytes: row sides (tiles x 2B FP64), split-row slots (2 per CTA, 2B
-// FP64 each), the column sides of the largest band (2B elem each) and, when
-// banded, the FP64 column accumulators (tiles x 2B).  Offsets in bytes.
+// FP64 each), the column sides (of all off-diagonal tile pairs, or of the
+// largest band, 2B elem each) and, when banded, the FP64 column accumulators
+// (tiles x 2B).  A banded product keeps two sets of slots and column sides,
+// so that consecutive bands can run at the same time.  Offsets in bytes.
 struct SymLayout {
     int64_t islots, jpart, colacc, bytes;
+    int64_t islots_stride, jpart_stride;   // bytes between the two sets (banded)
 };
 inline int64_t sym_r256(int64_t b) { return (b + 255) / 256 * 256; }
 inline SymLayout sym_layout(const SymPlan &pl, int B, int elem, int64_t slots, bool banded) {
+    const int nbuf = banded ? 2 : 1;
     SymLayout l;
     l.islots = sym_r256(pl.tiles * 2 * B * (int64_t)sizeof(double));
-    l.jpart = l.islots + sym_r256(pl.ctas * 4 * B * (int64_t)sizeof(double));
-    l.colacc = l.jpart + sym_r256(slots * 2 * B * (int64_t)elem);
+    l.islots_stride = sym_r256(pl.ctas * 4 * B * (int64_t)sizeof(double));
+    l.jpart = l.islots + nbuf * l.islots_stride;
+    l.jpart_stride = sym_r256(slots * 2 * B * (int64_t)elem);
+    l.colacc = l.jpart + nbuf * l.jpart_stride;
     l.bytes = l.colacc + (banded ? sym_r256(pl.tiles * 2 * B * (int64_t)sizeof(double)) : 0);
     return l;
 }
@@ -198,21 +204,46 @@ inline SymPlan sym_band_plan(const SymPlan &full, int64_t R0, int64_t R1) {
     return b;
 }
 
-// Band cuts 0 = R_0 < R_1 < ... < R_m = tiles under a scratch bound of
-// limit bytes (0: one band): the bound's room for column sides split into
-// about equal bands of whole row tiles, each at most that room, or one row
-// tile where a single row's column sides exceed it.
-inline void sym_band_cuts(const SymPlan &pl, int B, int elem, int64_t limit, std::vector<int64_t> *cuts) {
+// Bands split off for speed (bands = 0): the pair kernel of one launch ends
+// on a tail of CTAs finishing at different times, which the next band's
+// launch on the other stream fills.  As many bands as give every CTA at
+// least kBandMinPairs tile pairs each, at most kBandMaxAuto (measured on
+// GB300: 81,920 triangles 1295 -> 1337 Gpairs/s at 6 bands, 2572 -> 2731
+// with kappa = 0; 300,176 triangles 1317 -> 1402 at 14 to 36 bands, the
+// scratch 0.68 GB -> about 85 MB at 24; bands of 2 tile pairs per CTA lose
+// again for kappa = 0).
+constexpr int64_t kBandMinPairs = 5;
+constexpr int64_t kBandMaxAuto = 24;
+
+// Band cuts 0 = R_0 < R_1 < ... < R_m = tiles: whole row tiles holding about
+// equal numbers of column sides, at most the room that the scratch bound
+// limit leaves (bytes, 0: no bound; two sets of column sides) and at most
+// total / n for n requested bands: bands = 0 for the automatic split above,
+// 1 for none, n >= 2 for at least n.  Without a request of n >= 2 the product
+// takes one band whenever bands would not need less scratch.  A row tile whose
+// column sides alone exceed the room is a band of its own.
+inline void sym_band_cuts(const SymPlan &pl, int B, int elem, int64_t limit, int bands,
+                          std::vector<int64_t> *cuts) {
     const int64_t tiles = pl.tiles, total = sym_band_slots(tiles, 0, tiles);
+    const int64_t unbanded = sym_layout(pl, B, elem, total, false).bytes;
     cuts->clear();
     cuts->push_back(0);
-    int64_t room = 0;
-    if (limit > 0) {
+    int64_t room = total + 1;                     // no constraint
+    if (limit > 0 && unbanded > limit) {
         const SymLayout fixed = sym_layout(pl, B, elem, 0, true);
-        room = (limit - fixed.bytes) / (2 * B * (int64_t)elem);
-        if (room < 1) room = 1;
+        const int64_t r = (limit - fixed.bytes) / (2 * 2 * B * (int64_t)elem);
+        room = r < 1 ? 1 : r;
     }
-    if (limit <= 0 || total <= room) {
+    int64_t want = bands >= 2 ? bands : 1;
+    if (bands == 0) {
+        want = (pl.work / (pl.ctas > 0 ? pl.ctas : 1)) / kBandMinPairs;
+        if (want > kBandMaxAuto) want = kBandMaxAuto;
+    }
+    if (want >= 2) {
+        const int64_t r = (total + want - 1) / want;
+        if (r < room) room = r < 1 ? 1 : r;
+    }
+    if (total <= room) {
         cuts->push_back(tiles);
         return;
     }
@@ -223,6 +254,17 @@ inline void sym_band_cuts(const SymPlan &pl, int B, int elem, int64_t limit, std
         while (R1 < tiles && sym_band_slots(tiles, R0, R1 + 1) <= target) ++R1;
         cuts->push_back(R1);
         R0 = R1;
+    }
+    if (bands < 2) {
+        int64_t m = 0;
+        for (size_t b = 0; b + 1 < cuts->size(); ++b) {
+            const int64_t sl = sym_band_slots(tiles, (*cuts)[b], (*cuts)[b + 1]);
+            if (sl > m) m = sl;
+        }
+        if (sym_layout(pl, B, elem, m, true).bytes >= unbanded) {
+            cuts->resize(1);
+            cuts->push_back(tiles);
+        }
     }
 }
 
@@ -236,37 +278,56 @@ inline int64_t sym_max_band_slots(int64_t tiles, const std::vector<int64_t> &cut
     return m;
 }
 
-// Enqueue one symmetric product: pair(plan, islots, iside, jpart, evaluated)
-// launches the pair kernel over the plan's tile pairs, then the finishing
-// kernel runs; with more than one band, per band in order.  The product
-// counter is passed to the first band's pair kernel only.  Counts every
+// Enqueue one symmetric product: pair(plan, islots, iside, jpart, evaluated,
+// stream) launches the pair kernel over the plan's tile pairs, then the
+// finishing kernel runs.  With more than one band, band b runs on st (b even)
+// or aux (b odd) with set b % 2 of the slots and column sides: the pair
+// kernel of band b + 1 overlaps the end of band b's (whose last CTAs leave
+// SMs idle), the finishing kernels run in band order (each waits for the
+// previous one: the column accumulators), and a set is reused by the same
+// stream two bands later.  ev: three events; aux joins st at the end.  The
+// product counter goes to the first band's pair kernel only.  Counts every
 // launch but one (the caller counts the product's first).
 template <int B, typename JT, typename Pair>
-void sym_enqueue(const SymPlan &sp, const std::vector<int64_t> &cuts, void *scratch, const double *u, int64_t N,
-                 double diag1, double diag2, double *y, const int *skip, unsigned long long *counter,
-                 cudaStream_t st, Pair pair) {
+cudaError_t sym_enqueue(const SymPlan &sp, const std::vector<int64_t> &cuts, void *scratch, const double *u,
+                        int64_t N, double diag1, double diag2, double *y, const int *skip,
+                        unsigned long long *counter, cudaStream_t st, cudaStream_t aux, cudaEvent_t *ev,
+                        Pair pair) {
     const bool banded = cuts.size() > 2;
     const SymLayout l = sym_layout(sp, B, (int)sizeof(JT), banded ? sym_max_band_slots(sp.tiles, cuts) : 0, banded);
     char *base = (char *)scratch;
-    double *iside = (double *)base, *islots = (double *)(base + l.islots);
-    JT *jpart = (JT *)(base + l.jpart);
+    double *iside = (double *)base;
     if (!banded) {
-        pair(sp, islots, iside, jpart, counter);
+        double *islots = (double *)(base + l.islots);
+        JT *jpart = (JT *)(base + l.jpart);
+        pair(sp, islots, iside, jpart, counter, st);
         matvec_sym_finalize<B, JT><<<dim3((unsigned)sp.tiles, B / kSymFinRows), kSymFinThreads, 0, st>>>(
             u, N, diag1, diag2, sp, islots, iside, jpart, y, skip);
         PB_LAUNCHED();
-        return;
+        return cudaSuccess;
     }
     double *colacc = (double *)(base + l.colacc);
-    for (size_t b = 0; b + 1 < cuts.size(); ++b) {
+    cudaError_t e = cudaEventRecord(ev[2], st);            // the product's inputs are ready on st
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev[2], 0);
+    const size_t nb = cuts.size() - 1;
+    for (size_t b = 0; b < nb && e == cudaSuccess; ++b) {
         const int64_t R0 = cuts[b], R1 = cuts[b + 1];
         const SymPlan bp = sym_band_plan(sp, R0, R1);
-        pair(bp, islots, iside, jpart, b == 0 ? counter : nullptr);
+        cudaStream_t s = (b & 1) ? aux : st;
+        double *islots = (double *)(base + l.islots + (int64_t)(b & 1) * l.islots_stride);
+        JT *jpart = (JT *)(base + l.jpart + (int64_t)(b & 1) * l.jpart_stride);
+        pair(bp, islots, iside, jpart, b == 0 ? counter : nullptr, s);
         if (b > 0) PB_LAUNCHED();
-        matvec_sym_band_finish<B, JT><<<dim3((unsigned)(sp.tiles - R0), B / kSymFinRows), kSymFinThreads, 0, st>>>(
+        if (b > 0) e = cudaStreamWaitEvent(s, ev[(b - 1) & 1], 0);
+        if (e != cudaSuccess) break;
+        matvec_sym_band_finish<B, JT><<<dim3((unsigned)(sp.tiles - R0), B / kSymFinRows), kSymFinThreads, 0, s>>>(
             u, N, diag1, diag2, bp, R0, R1, islots, iside, jpart, colacc, y, skip);
         PB_LAUNCHED();
+        e = cudaEventRecord(ev[b & 1], s);
     }
+    // the last finishing kernel follows every other launch of the product
+    if (e == cudaSuccess && ((nb - 1) & 1)) e = cudaStreamWaitEvent(st, ev[(nb - 1) & 1], 0);
+    return e;
 }
 
 }  // namespace

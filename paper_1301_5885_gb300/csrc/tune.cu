@@ -58,7 +58,7 @@ int64_t default_scratch_bytes(int64_t n, int num_sms) {
     const int tile = kF32Threads * f32_variant_targets(v);
     std::vector<int64_t> cuts;
     return sym_scratch_need(make_sym_plan(n, tile, (int64_t)num_sms * 4), tile, (int)sizeof(float),
-                            kDefaultScratchLimit, &cuts);
+                            kDefaultScratchLimit, 0, &cuts);
 }
 
 void default_f32_config(pb_ctx *ctx, int *variant, int *ctas_per_sm) {
@@ -121,6 +121,13 @@ pb_status pb_set_scratch_limit(pb_ctx *ctx, int64_t bytes) {
     return PB_OK;
 }
 
+pb_status pb_set_bands(pb_ctx *ctx, int bands) {
+    if (!ctx) return set_error(nullptr, PB_ERR_ARG, "pb_set_bands: NULL context");
+    if (bands < 0) return set_error(ctx, PB_ERR_ARG, "pb_set_bands: negative band count %d", bands);
+    ctx->bands = bands;
+    return PB_OK;
+}
+
 pb_status pb_scratch_plan(pb_ctx *ctx, pb_precision prec, int *bands, int64_t *bytes) {
     if (!ctx) return set_error(nullptr, PB_ERR_ARG, "pb_scratch_plan: NULL context");
     std::vector<int64_t> cuts;
@@ -128,11 +135,11 @@ pb_status pb_scratch_plan(pb_ctx *ctx, pb_precision prec, int *bands, int64_t *b
     if (prec == PB_FP32PAIR) {
         if (f32_variant_symmetric(ctx->f32_variant))
             need = sym_scratch_need(ctx->plansym, kF32Threads * f32_variant_targets(ctx->f32_variant),
-                                    (int)sizeof(float), ctx->scratch_limit, &cuts);
+                                    (int)sizeof(float), ctx->scratch_limit, ctx->bands, &cuts);
     } else if (prec == PB_FP64) {
         if (ctx->f64_variant != MV_F64_PLAIN)
             need = sym_scratch_need(ctx->plansym64, kF64Threads * (ctx->f64_variant == MV_F64_SYM_T2 ? 2 : 1),
-                                    (int)sizeof(double), ctx->scratch_limit, &cuts);
+                                    (int)sizeof(double), ctx->scratch_limit, ctx->bands, &cuts);
     } else if (prec == PB_FLOAT2) {
         need = ff_sym_scratch_need(ctx, &cuts);
     } else {

@@ -4,8 +4,9 @@
   latter at the benchmark's tol 1e-4) against the FP64 oracle energy stored in
   tests/golden/oracle_energies.json (written by tests/golden/make_golden.py).
 * Sampled rows of the product at 81,920 and ~300,000 triangles against the
-  oracle's rows, computed one by one on the host; at ~300,000 also the
-  default scratch bound's bands and the FP32-pair product under a 100 MiB one.
+  oracle's rows, computed one by one on the host; at ~300,000 the default
+  products run in bands, and the FP32-pair product is also checked in one
+  pass and under a 100 MiB scratch bound.
 """
 import json
 import os
@@ -106,18 +107,18 @@ def test_sampled_rows_at_full_size(which, sphere2):
             yh = y.cpu().numpy()
             assert_rows_close(yh[rows], yh[p.n + rows], r1, r2, tol, prec)
         if which == "protein300k":
-            # the default 1 GiB bound: the FP32-pair product in one pass, the FP64
-            # and float-float ones (twice the bytes per column side) in bands
-            gib = 1 << 30
-            assert pb.pb_scratch_plan(ctx, "fp32pair")[0] == 1
-            for prec in ("fp64", "float2"):
+            # the defaults (the products above): 24 automatic bands for each
+            # symmetric product, within the 1 GiB bound
+            for prec in ("fp32pair", "fp64", "float2"):
                 bands, nbytes = pb.pb_scratch_plan(ctx, prec)
-                assert bands > 1 and nbytes <= gib
-            # and the FP32-pair product under a 100 MiB bound
-            pb.pb_set_scratch_limit(ctx, 100 << 20)
-            bands, nbytes = pb.pb_scratch_plan(ctx, "fp32pair")
-            assert bands > 1 and nbytes <= 100 << 20
-            pb.pb_matvec(ctx, ud, y, "fp32pair")
-            torch.cuda.synchronize()
-            yh = y.cpu().numpy()
-            assert_rows_close(yh[rows], yh[p.n + rows], r1, r2, TOL_FP32PAIR, "fp32pair banded")
+                assert bands >= 24 and nbytes <= 1 << 30
+            # one pass, and the FP32-pair product under a 100 MiB bound
+            for bands_req, limit in ((1, 0), (0, 100 << 20)):
+                pb.pb_set_bands(ctx, bands_req)
+                pb.pb_set_scratch_limit(ctx, limit)
+                bands, nbytes = pb.pb_scratch_plan(ctx, "fp32pair")
+                assert (bands == 1) if bands_req == 1 else (bands > 1 and nbytes <= limit)
+                pb.pb_matvec(ctx, ud, y, "fp32pair")
+                torch.cuda.synchronize()
+                yh = y.cpu().numpy()
+                assert_rows_close(yh[rows], yh[p.n + rows], r1, r2, TOL_FP32PAIR, f"fp32pair {bands} bands")
