@@ -390,6 +390,18 @@ pb_status pb_matvec_configure_fp64(pb_ctx *ctx, int variant, int *variant_out);
 pb_status pb_set_scratch_limit(pb_ctx *ctx, int64_t bytes);
 pb_status pb_set_bands(pb_ctx *ctx, int bands);
 
+/* The band plan of a symmetric product without a context (host only, no
+ * GPU): n targets in square tiles of `tile` targets (a multiple of 128),
+ * `ctas` persistent CTAs, column sides of elem bytes (4: FP32 pairs, 8: FP64
+ * and float-float), a scratch bound `limit` (0: none) and a band request as
+ * for pb_set_bands.  cuts receives up to max_cuts row-tile boundaries
+ * 0 = R_0 < R_1 < ... < R_m = tiles (band k holds row tiles [R_k, R_k+1));
+ * *ncuts = m + 1 and *bytes = the scratch (either may be NULL).  This is the
+ * plan pb_matvec uses for a context with that kernel choice, bound and
+ * request.  Bad arguments: PB_ERR_ARG. */
+pb_status pb_sym_band_plan(int64_t n, int tile, int64_t ctas, int elem, int64_t limit, int bands,
+                           int64_t *cuts, int max_cuts, int *ncuts, int64_t *bytes);
+
 /* Bands and scratch bytes of the symmetric product of precision prec at the
  * context's current kernel choice, bound and band request; 0 and 0 when that
  * product is not a symmetric one.  Either pointer may be NULL.  Unknown prec:

@@ -10,7 +10,7 @@ from ._ffi import (PB_ERR_ADMIT, PB_ERR_ARG, PB_ERR_BADMESH, PB_ERR_CUDA, PB_ERR
                    pb_energy_of, pb_get_info, pb_kernel_launches, pb_last_error, pb_matvec, pb_matvec_f32_static, pb_matvec_rows,
                    pb_matvec_autotune, pb_matvec_configure, pb_matvec_configure_fp64, pb_matvec_get_config, pb_profile_enable,
                    pb_profile_read, pb_release_cached_memory, pb_scratch_plan, pb_set_bands, pb_set_charges,
-                   pb_set_scratch_limit, pb_shard_rows,
+                   pb_set_scratch_limit, pb_shard_rows, pb_sym_band_plan,
                    pb_shard_unpack_host, pb_solve_sharded,
                    pb_solve, pb_source, pb_status_string)
 from . import build as build_module  # noqa: F401

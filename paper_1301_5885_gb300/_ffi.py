@@ -106,6 +106,8 @@ SIGNATURES = {
     "pb_matvec_configure_fp64": (_I, [_VP, _I, ctypes.POINTER(_I)]),
     "pb_set_scratch_limit": (_I, [_VP, _I64]),
     "pb_set_bands": (_I, [_VP, _I]),
+    "pb_sym_band_plan": (_I, [_I64, _I, _I64, _I, _I64, _I, ctypes.POINTER(_I64), _I, ctypes.POINTER(_I),
+                              ctypes.POINTER(_I64)]),
     "pb_scratch_plan": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I64)]),
     "pb_matvec_rows": (_I, [_VP, _VP, _VP, _I64, _I64, _I]),
     "pb_solve_sharded": (_I, [_VP, ctypes.POINTER(_Opts), _I, _I, _VP, _VP, _VP, _VP, ctypes.POINTER(_Info)]),
@@ -457,6 +459,17 @@ def pb_set_bands(ctx: Context, bands: int) -> None:
     """Bands of the symmetric products: 0 automatic (the default), 1 none,
     n >= 2 at least n."""
     _check(lib().pb_set_bands(ctx.handle, int(bands)), ctx)
+
+
+def pb_sym_band_plan(n: int, tile: int, ctas: int, elem: int, limit: int = 0, bands: int = 0):
+    """(row-tile cuts, scratch bytes) of a symmetric product's band plan,
+    computed on the host without a context (see include/pb.h)."""
+    tiles = -(-int(n) // int(tile))
+    buf = (_I64 * (tiles + 2))()
+    nc, nb = ctypes.c_int(), ctypes.c_int64()
+    _check(lib().pb_sym_band_plan(int(n), int(tile), int(ctas), int(elem), int(limit), int(bands), buf,
+                                  tiles + 2, ctypes.byref(nc), ctypes.byref(nb)))
+    return [buf[k] for k in range(nc.value)], nb.value
 
 
 def pb_scratch_plan(ctx: Context, prec="fp32pair"):

@@ -1166,3 +1166,17 @@ pb_status matvec_configure(pb_ctx *ctx, int variant, int ctas_per_sm) {
 }
 
 }  // namespace pb
+
+extern "C" pb_status pb_sym_band_plan(int64_t n, int tile, int64_t ctas, int elem, int64_t limit, int bands,
+                                      int64_t *cuts, int max_cuts, int *ncuts, int64_t *bytes) {
+    if (n < 1 || tile < 128 || tile % 128 != 0 || ctas < 1 || (elem != 4 && elem != 8) || limit < 0 || bands < 0 ||
+        max_cuts < 0 || (max_cuts > 0 && cuts == nullptr))
+        return pb::set_error(nullptr, PB_ERR_ARG, "pb_sym_band_plan: bad argument");
+    const pb::SymPlan pl = pb::make_sym_plan(n, tile, ctas);
+    std::vector<int64_t> c;
+    const int64_t need = pb::sym_scratch_need(pl, tile, elem, limit, bands, &c);
+    for (int k = 0; k < max_cuts && k < (int)c.size(); ++k) cuts[k] = c[k];
+    if (ncuts) *ncuts = (int)c.size();
+    if (bytes) *bytes = need;
+    return PB_OK;
+}
