@@ -327,6 +327,10 @@ cudaError_t sym_enqueue(const SymPlan &sp, const std::vector<int64_t> &cuts, voi
     }
     // the last finishing kernel follows every other launch of the product
     if (e == cudaSuccess && ((nb - 1) & 1)) e = cudaStreamWaitEvent(st, ev[(nb - 1) & 1], 0);
+    if (e != cudaSuccess) {
+        // join whatever reached the second stream before reporting the error
+        if (cudaEventRecord(ev[2], aux) == cudaSuccess) cudaStreamWaitEvent(st, ev[2], 0);
+    }
     return e;
 }
 
