@@ -194,9 +194,14 @@ pb_status pb_profile_read(pb_ctx *ctx, double *matvec_ms, int64_t *timed_launche
  * persistent launch over all surfaces that evaluates K1..K4 once per pair for
  * all charge sets of a surface; a surface with a single charge set whose
  * context is configured for a symmetric product variant (the default for
- * N >= 16,384) takes its own launch of that product instead.  All work runs
- * on ctxs[0]'s stream; the other
- * contexts must not be in use meanwhile.  use_graph = 1 captures one restart
+ * N >= 16,384) takes its own launch of that product instead.  The members
+ * are split into two halves of about equal pair work, each run by its own
+ * engine: one on ctxs[0]'s stream, one on a second stream of the same
+ * priority created for the call (it waits for the work enqueued on ctxs[0]'s
+ * stream before the call, and the call returns after both are done), their
+ * restart cycles launched together so that each fills the SMs the other's
+ * launches leave idle (pb_batch_set_streams(1): one engine on ctxs[0]'s
+ * stream).  The other contexts must not be in use meanwhile.  use_graph = 1 captures one restart
  * cycle of the whole batch in a CUDA graph and replays it (ignored on the
  * legacy default stream); 0 launches the kernels one by one; 2 launches them
  * one by one and times every product launch with CUDA events (matvec_ms).
@@ -227,11 +232,15 @@ typedef struct {
     double setup_ms;        /* host time of the set-up: vectors, source terms, norms */
     double cycles_ms;       /* host time of the restart cycles (tuning included) */
     double energy_ms;       /* host time of the energies (Eq. (14), FP64) */
+    int streams;            /* engines (streams) the call ran: 1 or 2 */
 } pb_batch_info;
 
 pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double *const *charges, const int64_t *nc,
                          const int *nrhs, const pb_solve_opts *opts, int use_graph, double *energies,
                          pb_batch_info *info);
+/* Engines of pb_batch_solve: 2 (default; one engine when nsurf is 1) or 1.
+ * Other n: PB_ERR_ARG. */
+pb_status pb_batch_set_streams(int n);
 
 /* Shapes of the batched product (a library extension; the paper has a single
  * one-target-per-thread kernel).  A shape is (targets per thread, row sums):

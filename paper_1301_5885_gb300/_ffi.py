@@ -46,7 +46,7 @@ class _BatchInfo(ctypes.Structure):
                 ("matvec_ms", ctypes.c_double), ("targets_per_thread", ctypes.c_int), ("row_sums", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("tuned", ctypes.c_int), ("tune_candidates", ctypes.c_int),
                 ("tune_ms", ctypes.c_double), ("setup_ms", ctypes.c_double), ("cycles_ms", ctypes.c_double),
-                ("energy_ms", ctypes.c_double)]
+                ("energy_ms", ctypes.c_double), ("streams", ctypes.c_int)]
 
 
 class _ServerOpts(ctypes.Structure):
@@ -114,6 +114,7 @@ SIGNATURES = {
     "pb_shard_rows": (_I, [_I64, _I, _I, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "pb_shard_unpack_host": (_I, [_VP, _I64, _I, _VP]),
     "pb_batch_set_tuning": (_I, [_I]),
+    "pb_batch_set_streams": (_I, [_I]),
     "pb_batch_force_shape": (_I, [_I, _I, _I, _I]),
     "pb_batch_clear_tuning": (_I, []),
     "pb_batch_shapes": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), _I]),
@@ -520,6 +521,11 @@ def pb_batch_solve(ctxs, charge_sets, restart: int = 10, tol: float = 1e-4, maxi
     d = {f: getattr(info, f) for f, _ in _BatchInfo._fields_}
     d["status"] = st
     return out, d
+
+
+def pb_batch_set_streams(n: int) -> None:
+    """Engines (streams) of pb_batch_solve: 2 (default) or 1."""
+    _check(lib().pb_batch_set_streams(int(n)))
 
 
 def pb_batch_set_tuning(autotune: bool) -> None:

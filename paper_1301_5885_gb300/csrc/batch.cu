@@ -22,8 +22,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -339,6 +342,7 @@ Engine::~Engine() {
     if (graph_) cudaGraphDestroy(graph_);
     cudaStreamSynchronize(stream_);
     if (h_status_) cudaFreeHost(h_status_);
+    if (h_evals_) cudaFreeHost(h_evals_);
     for (cudaEvent_t e : ev_) cudaEventDestroy(e);
 }
 
@@ -870,9 +874,33 @@ void Engine::enqueue_cycle() {
     cycle_kernels_ += 3;
 }
 
-pb_status Engine::cycle(bool use_graph, bool time_products) {
+pb_status Engine::prepare() {
     pb_status s = PB_OK;
     if (dirty_ && (s = rebuild()) != PB_OK) return s;
+    if (cap_h_evals_ < (size_t)nsurf_) {
+        if (h_evals_) {
+            cudaStreamSynchronize(stream_);
+            cudaFreeHost(h_evals_);
+            h_evals_ = nullptr;
+            cap_h_evals_ = 0;
+        }
+        const size_t cap = (size_t)nsurf_ + 16;
+        cudaError_t e = cudaMallocHost((void **)&h_evals_, cap * sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(e, "engine pinned counters");
+        cap_h_evals_ = cap;
+    }
+    return PB_OK;
+}
+
+pb_status Engine::cycle(bool use_graph, bool time_products) {
+    pb_status s = launch_cycle(use_graph, time_products);
+    return s != PB_OK ? s : finish_cycle();
+}
+
+pb_status Engine::launch_cycle(bool use_graph, bool time_products) {
+    pb_status s = prepare();
+    if (s != PB_OK) return s;
+    launched_ = false;
     if (nsurf_ == 0) return PB_OK;
     cudaError_t e = cudaSuccess;
     if (time_products) {
@@ -912,10 +940,17 @@ pb_status Engine::cycle(bool use_graph, bool time_products) {
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_status_, d_status_, nq_ * sizeof(BStatus), cudaMemcpyDeviceToHost, stream_);
-    std::vector<unsigned long long> ev(nsurf_, 0ull);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ev.data(), evals_, nsurf_ * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream_);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+        e = cudaMemcpyAsync(h_evals_, evals_, nsurf_ * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream_);
+    if (e != cudaSuccess) return cuda_fail(e, "engine cycle");
+    launched_ = true;
+    return PB_OK;
+}
+
+pb_status Engine::finish_cycle() {
+    if (!launched_) return PB_OK;
+    launched_ = false;
+    cudaError_t e = cudaStreamSynchronize(stream_);
     if (e != cudaSuccess) return cuda_fail(e, "engine cycle");
     for (int i = 0; timing_ && i + 1 < ev_used_; i += 2) {
         float ms = 0.f;
@@ -927,9 +962,9 @@ pb_status Engine::cycle(bool use_graph, bool time_products) {
     for (int si = 0; si < nsurf_; ++si) {
         EngineMember *mb = members_[surf_member_[si]];
         const int64_t pairs = mb->surf->N * (mb->surf->N - 1);
-        pair_evals += (int64_t)(ev[si] - last_evals_[si]) * pairs;
-        pair_products += (int64_t)(ev[si] - last_evals_[si]) * pairs * mb->nrhs;
-        last_evals_[si] = ev[si];
+        pair_evals += (int64_t)(h_evals_[si] - last_evals_[si]) * pairs;
+        pair_products += (int64_t)(h_evals_[si] - last_evals_[si]) * pairs * mb->nrhs;
+        last_evals_[si] = h_evals_[si];
         bool all = true;
         for (int r = 0; r < mb->nrhs; ++r, ++q) {
             mb->status[r] = h_status_[q];
@@ -977,6 +1012,10 @@ pb_status Engine::energies(EngineMember *mb, double *out) {
 // ---------------------------------------------------------------------------
 using namespace pb;
 
+namespace {
+std::atomic<int> g_batch_streams{2};   // engines (streams) of pb_batch_solve
+}  // namespace
+
 extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double *const *charges, const int64_t *nc,
                                     const int *nrhs, const pb_solve_opts *opts, int use_graph, double *energies,
                                     pb_batch_info *info) {
@@ -1005,35 +1044,105 @@ extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double
             return set_error(lead, PB_ERR_ARG, "pb_batch_solve: bad charges for surface %d", s);
     }
     const double t_begin = wall_seconds();
-    Engine eng(lead->stream, lead->device, lead->num_sms, o.restart, o.tol, o.maxit);
-    eng.autotune = true;
+    // Two engines on two streams (the members split in two halves of about
+    // equal pair work) run their restart cycles at the same time, so that one
+    // engine's launches fill the SMs the other's leave idle (the tail of each
+    // persistent product launch, the short orthogonalisation kernels).
+    const int neng = (g_batch_streams >= 2 && nsurf >= 2) ? 2 : 1;
+    cudaStream_t side = nullptr;
+    if (neng == 2) {
+        int prio = 0;
+        cudaError_t e = lead->stream ? cudaStreamGetPriority(lead->stream, &prio) : cudaSuccess;
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio);
+        if (e != cudaSuccess) return cuda_error(lead, e, "pb_batch_solve: second stream");
+        // the inputs the caller enqueued on its stream come first
+        cudaEvent_t ready = nullptr;
+        e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ready, lead->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ready, 0);
+        if (ready) cudaEventDestroy(ready);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(side);
+            return cuda_error(lead, e, "pb_batch_solve: second stream");
+        }
+    }
+    std::vector<std::unique_ptr<Engine>> engs;
+    for (int k = 0; k < neng; ++k) {
+        engs.emplace_back(new Engine(k == 0 ? lead->stream : side, lead->device, lead->num_sms, o.restart, o.tol,
+                                     o.maxit));
+        engs.back()->autotune = true;
+    }
+    // members to engines: by pair work, largest first, each to the lighter engine
+    std::vector<int> owner(nsurf, 0);
+    if (neng == 2) {
+        std::vector<int> order(nsurf);
+        for (int i = 0; i < nsurf; ++i) order[i] = i;
+        auto work = [&](int i) { return (double)ctxs[i]->N * (double)ctxs[i]->N * (double)nrhs[i]; };
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+        double load[2] = {0.0, 0.0};
+        for (int i : order) {
+            const int k = load[1] < load[0] ? 1 : 0;
+            owner[i] = k;
+            load[k] += work(i);
+        }
+    }
     std::vector<EngineMember *> mem(nsurf, nullptr);
     pb_status s = PB_OK;
-    for (int i = 0; i < nsurf && s == PB_OK; ++i) mem[i] = eng.add(ctxs[i], charges[i], nc[i], nrhs[i], (uint64_t)i, &s);
-    if (s != PB_OK) return set_error(lead, s, "%s", eng.error);
+    for (int i = 0; i < nsurf && s == PB_OK; ++i)
+        mem[i] = engs[owner[i]]->add(ctxs[i], charges[i], nc[i], nrhs[i], (uint64_t)i, &s);
+    auto finish_engines = [&]() {
+        engs.clear();
+        if (side) {
+            cudaStreamSynchronize(side);
+            cudaStreamDestroy(side);
+            side = nullptr;
+        }
+    };
+    auto engine_error = [&]() -> const char * {
+        for (auto &e : engs)
+            if (e->error[0]) return e->error;
+        return "engine error";
+    };
+    if (s != PB_OK) {
+        set_error(lead, s, "%s", engine_error());
+        finish_engines();
+        return s;
+    }
     const double t_setup = wall_seconds();
     bool all = false;
     int tuned_any = 0, tune_candidates = 0;
     double tune_ms = 0.0;
     for (int cyc = 0; cyc < o.maxit + 2 && s == PB_OK && !all; ++cyc) {
-        s = eng.cycle(use_graph == 1, use_graph == 2);
-        if (eng.tuned) {
-            tuned_any = 1;
-            tune_candidates += eng.tune_candidates;
-            tune_ms += eng.tune_ms;
-            eng.tuned = false;
+        // tables and tuning first (nothing in flight), then both cycles at once
+        for (auto &e : engs)
+            if (s == PB_OK) s = e->prepare();
+        for (auto &e : engs)
+            if (s == PB_OK) s = e->launch_cycle(use_graph == 1, use_graph == 2);
+        for (auto &e : engs) {
+            const pb_status fs = e->finish_cycle();
+            if (s == PB_OK) s = fs;
+            if (e->tuned) {
+                tuned_any = 1;
+                tune_candidates += e->tune_candidates;
+                tune_ms += e->tune_ms;
+                e->tuned = false;
+            }
         }
         all = true;
         for (EngineMember *mb : mem) all &= mb->finished;
     }
-    if (s != PB_OK) return set_error(lead, s, "%s", eng.error);
+    if (s != PB_OK) {
+        set_error(lead, s, "%s", engine_error());
+        finish_engines();
+        return s;
+    }
     const double t_cycles = wall_seconds();
     int k = 0, nconv = 0, nq = 0, iters_max = 0;
     int64_t iters_sum = 0;
     double resid_max = 0.0;
     pb_status worst = PB_OK;
     for (int i = 0; i < nsurf && s == PB_OK; ++i) {
-        s = eng.energies(mem[i], energies + k);
+        s = engs[owner[i]]->energies(mem[i], energies + k);
         for (int r = 0; r < nrhs[i]; ++r) {
             const BStatus &b = mem[i]->status[r];
             nconv += b.converged;
@@ -1046,33 +1155,52 @@ extern "C" pb_status pb_batch_solve(pb_ctx *const *ctxs, int nsurf, const double
         }
         k += nrhs[i];
     }
-    if (s != PB_OK) return set_error(lead, s, "%s", eng.error);
+    if (s != PB_OK) {
+        set_error(lead, s, "%s", engine_error());
+        finish_engines();
+        return s;
+    }
     const double t_end = wall_seconds();
     if (info) {
+        const Engine &eng = *engs[0];
         info->setup_ms = 1e3 * (t_setup - t_begin);
         info->cycles_ms = 1e3 * (t_cycles - t_setup);
         info->energy_ms = 1e3 * (t_end - t_cycles);
         info->instances = nq;
         info->converged = nconv;
-        info->cycles = eng.cycles_run;
+        info->cycles = 0;
+        info->pair_evals = info->pair_products = info->matvec_launches = 0;
+        info->matvec_ms = 0.0;
+        info->rhs_width = 0;
+        for (auto &e : engs) {
+            info->cycles = e->cycles_run > info->cycles ? e->cycles_run : info->cycles;
+            info->pair_evals += e->pair_evals;
+            info->pair_products += e->pair_products;
+            info->matvec_launches += e->matvec_launches;
+            info->matvec_ms += e->matvec_ms;
+            info->rhs_width = e->rhs_width > info->rhs_width ? e->rhs_width : info->rhs_width;
+        }
         info->iters_max = iters_max;
         info->iters_sum = iters_sum;
         info->rel_resid_max = resid_max;
-        info->rhs_width = eng.rhs_width;
         info->ctas = eng.ctas;
-        info->pair_evals = eng.pair_evals;
-        info->pair_products = eng.pair_products;
-        info->matvec_launches = eng.matvec_launches;
-        info->matvec_ms = eng.matvec_ms;
         info->targets_per_thread = eng.config.T;
         info->row_sums = eng.config.acc;
         info->ctas_per_sm = eng.config.ctas_per_sm;
         info->tuned = tuned_any;
         info->tune_candidates = tune_candidates;
         info->tune_ms = tune_ms;
+        info->streams = neng;
     }
+    finish_engines();
     if (worst != PB_OK)
         return set_error(lead, worst, "pb_batch_solve: %d of %d instances did not converge", nq - nconv, nq);
+    return PB_OK;
+}
+
+extern "C" pb_status pb_batch_set_streams(int n) {
+    if (n != 1 && n != 2) return set_error(nullptr, PB_ERR_ARG, "pb_batch_set_streams: n must be 1 or 2");
+    g_batch_streams = n;
     return PB_OK;
 }
 

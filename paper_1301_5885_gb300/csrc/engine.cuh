@@ -62,6 +62,14 @@ class Engine {
     // time_products (no graph), the product launches are bracketed by CUDA
     // events and their time is added to matvec_ms.
     pb_status cycle(bool use_graph, bool time_products = false);
+    // The same in two halves, so that several engines on their own streams
+    // can run their cycles at the same time: prepare() rebuilds the tables
+    // (and tunes) if the member set changed, launch_cycle() enqueues the cycle
+    // and the copies of its results without waiting, finish_cycle() waits for
+    // them and updates the members.
+    pb_status prepare();
+    pb_status launch_cycle(bool use_graph, bool time_products = false);
+    pb_status finish_cycle();
     // Caps the batched product's CTAs per SM (0: no cap); takes effect at the
     // next cycle (the tables are rebuilt).
     void set_cta_cap(int cap) {
@@ -126,6 +134,9 @@ class Engine {
     size_t cap_surf_ = 0, cap_inst_ = 0, cap_ch_ = 0, cap_cnt_inst_ = 0, cap_cnt_tile_ = 0, cap_evals_ = 0,
            cap_flags_ = 0, cap_red_ = 0, cap_part_ = 0, cap_status_ = 0;
     std::vector<unsigned long long> last_evals_;
+    unsigned long long *h_evals_ = nullptr;   // pinned copy of the product counters
+    size_t cap_h_evals_ = 0;
+    bool launched_ = false;                   // a cycle was launched and not finished
     cudaGraphExec_t gexec_ = nullptr;
     cudaGraph_t graph_ = nullptr;
     int kernels_per_cycle_ = 0, mv_per_cycle_ = 0, cycle_kernels_ = 0, cycle_mv_ = 0;

@@ -180,3 +180,31 @@ def test_autotuned_batch_matches_the_default_and_the_oracle():
         for r, q in enumerate(sets):
             e = oracle.solve(p.surface, q, p.eps1, p.eps2, p.kappa, tol=1e-11)["energy"]
             assert es[r] == pytest.approx(e, rel=1e-5)
+
+
+def test_one_and_two_engines_give_the_same_energies():
+    """The members split over two engines on two streams (the default) and
+    all in one engine: the same energies within the FP32-pair tolerance (the
+    products' work splits differ), and a single surface takes one engine."""
+    pb = _pb()
+    mix = _mix()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctxs = [pb.pb_create(p.surface.centroids, p.surface.normals, p.surface.areas, sets[0], p.eps1, p.eps2,
+                             p.kappa, stream=stream) for p, sets in mix]
+        try:
+            sets = [s for _, s in mix]
+            e2, i2 = pb.pb_batch_solve(ctxs, sets, tol=1e-7, maxit=2000, use_graph=True)
+            pb.pb_batch_set_streams(1)
+            e1, i1 = pb.pb_batch_solve(ctxs, sets, tol=1e-7, maxit=2000, use_graph=True)
+            _, i_single = pb.pb_batch_solve(ctxs[:1], sets[:1], tol=1e-7, maxit=2000, use_graph=True)
+        finally:
+            pb.pb_batch_set_streams(2)
+            for c in ctxs:
+                pb.pb_destroy(c)
+    assert i2["streams"] == 2 and i1["streams"] == 1 and i_single["streams"] == 1
+    assert i2["converged"] == i2["instances"] == i1["converged"] == i1["instances"]
+    for a, b in zip(e2, e1):
+        assert a == pytest.approx(b, rel=2e-6, abs=1e-9)
+    with pytest.raises(pb.PBError):
+        pb.pb_batch_set_streams(3)
