@@ -972,7 +972,7 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         };                                                                                                      \
         sym_e = sym_enqueue<kF32Threads * T, float>(ctx->plansym, ctx->cuts32, ctx->sym_scratch, u, ctx->N,     \
                                                     diag1, diag2, y, skip_flag, ctx->mv_count, ctx->stream,    \
-                                                    ctx->band_aux(), ctx->band_ev, pair);                     \
+                                                    ctx->band_stream, ctx->band_ev, pair);                     \
     } while (0)
         switch (ctx->f32_variant) {
             case MV_F32_SCALAR_T4:
@@ -1010,12 +1010,12 @@ pb_status matvec_launch(pb_ctx *ctx, const double *u, double *y, pb_precision pr
         if (ctx->f64_variant == MV_F64_SYM_T2)
             sym_e = sym_enqueue<2 * kF64Threads, double>(ctx->plansym64, ctx->cuts64, ctx->sym64_scratch, u, ctx->N,
                                                          diag1, diag2, y, skip_flag, ctx->mv_count, ctx->stream,
-                                                         ctx->band_aux(), ctx->band_ev,
+                                                         ctx->band_stream, ctx->band_ev,
                                                          pair(std::integral_constant<int, 2>{}));
         else
             sym_e = sym_enqueue<kF64Threads, double>(ctx->plansym64, ctx->cuts64, ctx->sym64_scratch, u, ctx->N,
                                                      diag1, diag2, y, skip_flag, ctx->mv_count, ctx->stream,
-                                                     ctx->band_aux(), ctx->band_ev,
+                                                     ctx->band_stream, ctx->band_ev,
                                                      pair(std::integral_constant<int, 1>{}));
     }
     if (sym_e != cudaSuccess) return cuda_error(ctx, sym_e, "symmetric product bands");

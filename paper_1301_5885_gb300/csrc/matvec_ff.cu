@@ -596,11 +596,11 @@ pb_status matvec_ff_enqueue(pb_ctx *ctx, const double *u, double *y, const int *
     cudaError_t e;
     if (T == 2)
         e = sym_enqueue<2 * kFFThreads, double>(sp, ctx->cutsff, ctx->symff_scratch, u, ctx->N, prm.diag1, prm.diag2,
-                                                y, skip_flag, ctx->mv_count, ctx->stream, ctx->band_aux(),
+                                                y, skip_flag, ctx->mv_count, ctx->stream, ctx->band_stream,
                                                 ctx->band_ev, pair(std::integral_constant<int, 2>{}));
     else
         e = sym_enqueue<kFFThreads, double>(sp, ctx->cutsff, ctx->symff_scratch, u, ctx->N, prm.diag1, prm.diag2, y,
-                                            skip_flag, ctx->mv_count, ctx->stream, ctx->band_aux(), ctx->band_ev,
+                                            skip_flag, ctx->mv_count, ctx->stream, ctx->band_stream, ctx->band_ev,
                                             pair(std::integral_constant<int, 1>{}));
     return e == cudaSuccess ? PB_OK : cuda_error(ctx, e, "symmetric float-float product bands");
 }

@@ -189,13 +189,9 @@ struct pb_ctx {
     int64_t scratch_limit = pb::kDefaultScratchLimit;
     int bands = 0;                 // requested bands: 0 automatic, 1 none, n >= 2 at least n
     std::vector<int64_t> cuts32, cuts64, cutsff;
-    // second stream and events of a banded product (created by its first one);
-    // band_overlap false runs the bands one after another on the context's
-    // stream (the solve server, while the two lanes share the SMs)
+    // second stream and events of a banded product (created by its first one)
     cudaStream_t band_stream = nullptr;
     cudaEvent_t band_ev[3] = {nullptr, nullptr, nullptr};
-    bool band_overlap = true;
-    cudaStream_t band_aux() const { return band_overlap ? band_stream : stream; }
     unsigned int *tile_counters = nullptr;
     int64_t counters_len = 0;
 

@@ -170,13 +170,14 @@ void admit(pb_server *sv, Lane &L) {
 }
 
 // Large lane: while the small lane runs requests, symmetric products use one
-// CTA per SM fewer than their occupancy and run their bands one after another
-// on one stream (so small-lane kernels find slots).
+// CTA per SM fewer than their occupancy in one pass (no bands: the launches
+// of overlapping bands would take the slots), so small-lane kernels find
+// slots; otherwise their default bands.
 pb_status set_yield(Lane &L, bool yield) {
     for (Request *r : L.active) {
         pb_ctx *c = r->ctx;
         if (!c || !f32_variant_symmetric(c->f32_variant)) continue;
-        c->band_overlap = !yield;
+        c->bands = yield ? 1 : 0;
         const int occ = matvec_f32_occupancy(c->f32_variant);
         const int want = (yield && occ > 1) ? occ - 1 : 0;
         if (want == r->cps) continue;

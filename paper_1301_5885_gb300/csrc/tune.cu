@@ -56,9 +56,10 @@ int64_t default_scratch_bytes(int64_t n, int num_sms) {
     const int v = n >= kSymT4MinN ? MV_F32_SYM_T4 : (n >= kSymT2MinN ? MV_F32_SYM_T2 : 0);
     if (v == 0) return 0;
     const int tile = kF32Threads * f32_variant_targets(v);
+    // one pass (the solve server's large requests take it while the lanes share the SMs)
     std::vector<int64_t> cuts;
     return sym_scratch_need(make_sym_plan(n, tile, (int64_t)num_sms * 4), tile, (int)sizeof(float),
-                            kDefaultScratchLimit, 0, &cuts);
+                            kDefaultScratchLimit, 1, &cuts);
 }
 
 void default_f32_config(pb_ctx *ctx, int *variant, int *ctas_per_sm) {
