@@ -208,3 +208,25 @@ def test_one_and_two_engines_give_the_same_energies():
         assert a == pytest.approx(b, rel=2e-6, abs=1e-9)
     with pytest.raises(pb.PBError):
         pb.pb_batch_set_streams(3)
+
+
+def test_two_engines_from_the_legacy_default_stream():
+    """Contexts on the legacy default stream: the first engine launches its
+    kernels one by one there (no graph), the second runs on the call's own
+    stream; the energies equal the one-engine run's."""
+    pb = _pb()
+    mix = _mix()[:4]
+    ctxs = [pb.pb_create(p.surface.centroids, p.surface.normals, p.surface.areas, sets[0], p.eps1, p.eps2, p.kappa,
+                         stream=None) for p, sets in mix]
+    try:
+        sets = [s for _, s in mix]
+        e2, i2 = pb.pb_batch_solve(ctxs, sets, tol=1e-7, maxit=2000, use_graph=True)
+        pb.pb_batch_set_streams(1)
+        e1, _ = pb.pb_batch_solve(ctxs, sets, tol=1e-7, maxit=2000, use_graph=True)
+    finally:
+        pb.pb_batch_set_streams(2)
+        for c in ctxs:
+            pb.pb_destroy(c)
+    assert i2["streams"] == 2 and i2["converged"] == i2["instances"]
+    for a, b in zip(e2, e1):
+        assert a == pytest.approx(b, rel=2e-6, abs=1e-9)
