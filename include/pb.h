@@ -19,8 +19,10 @@
  *  - Lengths in Angstrom, charges in e_c, energies in kcal/mol.
  *  - Vectors of length 2N are FP64, contiguous, device memory owned by the
  *    caller (for example a torch tensor's data_ptr()).
- *  - All GPU work of a context runs on the CUDA stream given to pb_create.
- *    pb_matvec and pb_source only enqueue work; pb_solve, pb_energy,
+ *  - All GPU work of a context is ordered on the CUDA stream given to
+ *    pb_create (a banded symmetric product forks part of its launches to a
+ *    second stream of the context and joins it back on that stream; see
+ *    pb_set_bands).  pb_matvec and pb_source only enqueue work; pb_solve, pb_energy,
  *    pb_energy_of and pb_create return after the stream has finished the work
  *    they enqueued.
  *  - Every call returns a pb_status and never aborts, traps or exits.  On
