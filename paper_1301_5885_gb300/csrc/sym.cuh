@@ -85,11 +85,12 @@ matvec_sym_finalize(const double *__restrict__ u, int64_t N, double diag1, doubl
     y[N + i] = diag2 * u[N + i] - s2;
 }
 
-// Banded form (a bound on the scratch).  The product runs as bands of whole
-// row tiles [R0, R1): the pair kernel evaluates the band's tile pairs (plan
-// with work_begin = sym_row_start(R0)) and stores only the band's column
-// sides; this kernel then finishes the band's rows and folds the band's column
-// sides of the later row tiles into FP64 accumulators colacc (tiles x 2B).
+// Banded form (the default for large N, see sym_band_cuts).  The product runs
+// as bands of whole row tiles [R0, R1): the pair kernel evaluates the band's
+// tile pairs (plan with work_begin = sym_row_start(R0)) and stores only the
+// band's column sides; this kernel then finishes the band's rows and folds
+// the band's column sides of the later row tiles into FP64 accumulators
+// colacc (tiles x 2B).
 // Block (R - R0, c), R in [R0, tiles), covers entries 64 c .. + 63 of tile R:
 // its four groups sum the band's column sides (I', R), I' = R0 + g, R0 + g + 4,
 // ... (I' < min(R, R1)), then
