@@ -66,7 +66,8 @@ typedef enum {
                              FP64 rate is a small fraction of FP32.  From
                              N = 2,048 each unordered pair is evaluated once
                              for both rows, with device scratch of about
-                             8 N^2 / 256 bytes allocated by the first such
+                             8 N^2 / 256 bytes in one pass (less in bands,
+                             see pb_set_bands) allocated by the first such
                              product.  Accepted by pb_matvec, pb_solve
                              (prec, refine_prec), pb_source and pb_energy_of
                              (the N x Nc pair sums of Eqs. (11) and (14)). */
@@ -340,8 +341,9 @@ void pb_server_destroy(pb_server *sv);
  * packed f32x2 with 2 and 4 targets per thread (each unordered pair of
  * Eqs. (12)-(13) evaluated once for both of its rows, using K1(i,j) = K1(j,i),
  * K4(i,j) = K4(j,i) and the sign change of c_x, c_y under the exchange; two
- * kernel launches per product; device scratch of about 4 N^2 / (128 t) bytes,
- * t the targets per thread, allocated by the first product that uses the
+ * kernel launches per product in one pass, two per band in bands (see
+ * pb_set_bands); device scratch of about 4 N^2 / (128 t) bytes in one pass,
+ * t the targets per thread, less in bands, allocated by the first product that uses the
  * variant and freed when another variant is configured; that product returns
  * PB_ERR_OOM if it cannot be allocated); 0 = the
  * stored or built-in default.  The packed variants use a kappa = 0
@@ -358,8 +360,9 @@ pb_status pb_matvec_autotune(pb_ctx *ctx, int reps, int *variant, int *ctas_per_
  * of the refinement in pb_solve).  variant: 1 = plain (every ordered pair);
  * 2 and 3 = symmetric with 1 and 2 targets per thread (each unordered pair of
  * Eqs. (12)-(13) evaluated once for both rows, as in the FP32-pair variants
- * 5 and 6, with FP64 column sides; scratch of about 8 N^2 / (128 t) bytes,
- * t the targets per thread, allocated by the first product and freed when
+ * 5 and 6, with FP64 column sides; scratch of about 8 N^2 / (128 t) bytes in
+ * one pass, t the targets per thread, less in bands (see pb_set_bands),
+ * allocated by the first product and freed when
  * the plain variant is configured); 0 = the built-in default for the
  * context's N (symmetric from N = 2,048, with 2 targets per thread from
  * 65,536; pb_create applies it).  All variants do every pair and every sum in FP64; results
