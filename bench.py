@@ -81,10 +81,11 @@ def matvec_peak_gpairs(ops_per_pair):
 # without the cache flush (as in a solve); a configuration not captured
 # reports no traffic
 MATVEC_TRAFFIC_BYTES = {
-    # profiles/matvec_sym_kernel_protein300k_traffic.md: one pass, and the
-    # default 25 bands (MB to 0.1 and 0.01)
+    # profiles/matvec_sym_kernel_protein300k_traffic.md: one pass, 25 bands,
+    # and the default 79 bands (MB to 0.1 and 0.01)
     ("matvec_sym_kernel<4> + finishing kernels", "protein300k", 1): (30.4 + 660.7 + 716.9 + 64.9) * 1e6,
     ("matvec_sym_kernel<4> + finishing kernels", "protein300k", 25): (13.54 + 453.29 + 1.74 + 78.41) * 1e6,
+    ("matvec_sym_kernel<4> + finishing kernels", "protein300k", 79): (6.64 + 13.33 + 0.08 + 6.73) * 1e6,
 }
 
 WORKLOADS = {

@@ -395,8 +395,9 @@ pb_status pb_matvec_configure_fp64(pb_ctx *ctx, int variant, int *variant_out);
  *
  * pb_set_bands: bands requested besides the bound.  0 (the default):
  * automatic, as many as give every CTA of the product's persistent grid at
- * least 5 tile pairs per band, at most 24 (for the FP32-pair product: one
- * pass below about 28,000 triangles, 6 bands at 81,920, about 24 at 300,000);
+ * least 5 tile pairs per band, at most 72 requested (for the FP32-pair
+ * product: one pass below about 28,000 triangles, 6 bands at 81,920, 79 at
+ * 300,176);
  * 1: none; n >= 2: at least n (or one row tile per band where the row
  * tiles are fewer).  Except for n >= 2, a product takes one pass
  * whenever bands would need more scratch than one pass.  Takes effect at the

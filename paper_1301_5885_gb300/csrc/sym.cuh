@@ -210,11 +210,12 @@ inline SymPlan sym_band_plan(const SymPlan &full, int64_t R0, int64_t R1) {
 // launch on the other stream fills.  As many bands as give every CTA at
 // least kBandMinPairs tile pairs each, at most kBandMaxAuto (measured on
 // GB300: 81,920 triangles 1295 -> 1337 Gpairs/s at 6 bands, 2572 -> 2731
-// with kappa = 0; 300,176 triangles 1317 -> 1402 at 14 to 36 bands, the
-// scratch 0.68 GB -> about 85 MB at 24; bands of 2 tile pairs per CTA lose
-// again for kappa = 0).
+// with kappa = 0; 300,176 triangles 1317 -> 1396..1402 at 14 to 79 bands;
+// at 79 bands (the cap's choice there) each band's column sides stay in L2
+// and the product moves 27 MB through DRAM instead of 1.47 GB, with 44 MB of
+// scratch; bands of 2 tile pairs per CTA lose again for kappa = 0).
 constexpr int64_t kBandMinPairs = 5;
-constexpr int64_t kBandMaxAuto = 24;
+constexpr int64_t kBandMaxAuto = 72;
 
 // Band cuts 0 = R_0 < R_1 < ... < R_m = tiles: whole row tiles holding about
 // equal numbers of column sides, at most the room that the scratch bound

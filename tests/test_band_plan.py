@@ -129,7 +129,7 @@ def _check_cuts(cuts, tiles):
 
 # ---- the plan ------------------------------------------------------------------
 @pytest.mark.parametrize("n,tile,ctas,bands_expected,bytes_expected", [
-    (300_176, 512, 456, 25, 83_238_912),     # the benchmark solute, default plan
+    (300_176, 512, 456, 79, 44_122_112),     # the benchmark solute, default plan
     (81_920, 512, 456, 6, 38_248_448),       # the 81,920-triangle sphere
     (20_416, 512, 456, 1, None),             # too little work per CTA for bands
 ])

@@ -107,11 +107,12 @@ def test_sampled_rows_at_full_size(which, sphere2):
             yh = y.cpu().numpy()
             assert_rows_close(yh[rows], yh[p.n + rows], r1, r2, tol, prec)
         if which == "protein300k":
-            # the defaults (the products above): 24 automatic bands for each
-            # symmetric product, within the 1 GiB bound
+            # the defaults (the products above): automatic bands for each
+            # symmetric product (79 for the FP32-pair one), within the 1 GiB bound
             for prec in ("fp32pair", "fp64", "float2"):
                 bands, nbytes = pb.pb_scratch_plan(ctx, prec)
-                assert bands >= 24 and nbytes <= 1 << 30
+                assert bands >= 72 and nbytes <= 1 << 30
+            assert pb.pb_scratch_plan(ctx, "fp32pair") == (79, 44_122_112)
             # one pass, and the FP32-pair product under a 100 MiB bound
             for bands_req, limit in ((1, 0), (0, 100 << 20)):
                 pb.pb_set_bands(ctx, bands_req)
